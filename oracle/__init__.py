@@ -1,0 +1,177 @@
+"""FP64 CPU oracle for FFT-based scalar diffraction (CWO++, Shimobaba et al.).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import this package; the product path never does.  It shares no code with
+the CUDA library.  The arithmetic lives in ``cwo_oracle.c`` (plain C, double precision); this
+module compiles it with gcc on first use and wraps it with ctypes.  The composites below (the
+z-stack and the hologram loss gradient) only call those C functions in the order the paper's
+usage describes.
+
+Pins (each checked by the ``-m "not gpu"`` tests, none of them by re-calling this code):
+  * ``fft``            -- direct DFT on every size 1..64 and numpy.fft as a third opinion
+  * ``dft``            -- closed forms: delta -> ones, pure tone -> scaled delta (fixes the sign)
+  * ``propagate``      -- Fresnel: brute-force direct sum and the Gaussian-beam closed form;
+                          ASM: brute-force kernel sum, plane-wave phase exp(ikz), z = 0 identity,
+                          Gaussian-beam Hankel quadrature, Parseval, z then -z
+  * adjoint flag       -- dot-product test <A x, y> = <x, A^H y>
+  * ``hologram_grad``  -- central finite differences
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cwo_oracle.c")
+_LIB = os.path.join(_HERE, "_cwo_oracle.so")
+
+# flag and type values of cwo_oracle.c
+ADJOINT = 1
+NO_PAD = 2
+FULL_OUTPUT = 4
+LITERAL_SCALE = 8
+ANGULAR = 0
+FRESNEL_CONV = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile cwo_oracle.c into _cwo_oracle.so with gcc (OpenMP on, IEEE arithmetic)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            dp = ctypes.c_void_p
+            L, D, I, U = ctypes.c_long, ctypes.c_double, ctypes.c_int, ctypes.c_uint
+            lib.orc_dft.argtypes = [dp, dp, L, I]
+            lib.orc_dft.restype = None
+            lib.orc_fft.argtypes = [dp, L, I]
+            lib.orc_fft.restype = I
+            lib.orc_fft2.argtypes = [dp, L, L, I]
+            lib.orc_fft2.restype = I
+            lib.orc_asm_transfer.argtypes = [dp, L, L, D, D, D, D]
+            lib.orc_asm_transfer.restype = None
+            lib.orc_propagate.argtypes = [dp, dp, L, L, D, D, D, D, I, U]
+            lib.orc_propagate.restype = I
+            lib.orc_propagate_direct.argtypes = [dp, dp, L, L, D, D, D, D, I, U]
+            lib.orc_propagate_direct.restype = I
+            lib.orc_max_threads.argtypes = []
+            lib.orc_max_threads.restype = I
+            _lib = lib
+    return _lib
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def max_threads() -> int:
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(_load().orc_max_threads())
+
+
+def dft(x, sign: int = -1) -> np.ndarray:
+    """Direct O(n^2) DFT, X[k] = sum_j x[j] exp(sign 2 pi i j k / n)."""
+    x = _c128(x)
+    out = np.empty_like(x)
+    _load().orc_dft(x.ctypes.data, out.ctypes.data, x.size, sign)
+    return out
+
+
+def fft(x, sign: int = -1) -> np.ndarray:
+    """Textbook radix-2 FFT (unscaled)."""
+    a = _c128(x).copy()
+    if _load().orc_fft(a.ctypes.data, a.size, sign) != 0:
+        raise ValueError("orc_fft: length must be a power of two")
+    return a
+
+
+def fft2(x, sign: int = -1) -> np.ndarray:
+    a = _c128(x).copy()
+    if _load().orc_fft2(a.ctypes.data, a.shape[0], a.shape[1], sign) != 0:
+        raise ValueError("orc_fft2: sides must be powers of two")
+    return a
+
+
+def asm_transfer(px: int, py: int, dx: float, dy: float, lam: float, z: float) -> np.ndarray:
+    """H_A of Eq. ang2 on the [py][px] frequency grid (0 where evanescent)."""
+    H = np.empty((py, px), dtype=np.complex128)
+    _load().orc_asm_transfer(H.ctypes.data, px, py, dx, dy, lam, z)
+    return H
+
+
+def propagate(u1, dx: float, dy: float, lam: float, z: float, kind: int = ANGULAR,
+              flags: int = 0) -> np.ndarray:
+    """Pad, FFT, multiply by H, inverse FFT, crop (one [ny][nx] field, complex128)."""
+    u1 = _c128(u1)
+    ny, nx = u1.shape
+    shape = (2 * ny, 2 * nx) if (flags & FULL_OUTPUT and not flags & NO_PAD) else (ny, nx)
+    u2 = np.empty(shape, dtype=np.complex128)
+    st = _load().orc_propagate(u1.ctypes.data, u2.ctypes.data, nx, ny, dx, dy, lam, z, kind, flags)
+    if st != 0:
+        raise ValueError(f"orc_propagate failed with status {st}")
+    return u2
+
+
+def propagate_direct(u1, dx: float, dy: float, lam: float, z: float, kind: int = ANGULAR,
+                     flags: int = 0) -> np.ndarray:
+    """Brute-force linear-convolution sum (tiny grids, N <= 64)."""
+    u1 = _c128(u1)
+    ny, nx = u1.shape
+    u2 = np.empty_like(u1)
+    st = _load().orc_propagate_direct(u1.ctypes.data, u2.ctypes.data, nx, ny, dx, dy, lam, z, kind, flags)
+    if st != 0:
+        raise ValueError(f"orc_propagate_direct failed with status {st}")
+    return u2
+
+
+def propagate_stack(u1, dx: float, dy: float, lam: float, zs, kind: int = ANGULAR,
+                    flags: int = 0) -> np.ndarray:
+    """3-D field by stacking 2-D diffractions along z (Section "Three-dimensional diffraction
+    calculations"): one independent propagation of the same source per plane."""
+    return np.stack([propagate(u1, dx, dy, lam, float(z), kind, flags) for z in zs])
+
+
+def hologram_loss_grad(phi, canvas: tuple, offset: tuple, target, dx: float, lam: float,
+                       z: float):
+    """Loss and gradient of the phase-only hologram objective.
+
+    x = exp(i phi) placed at ``offset`` (row, col) inside a zero canvas, U = A x with A the
+    padded angular-spectrum propagation, loss L = mean over the phi-sized window of
+    (|U|^2 - T)^2.  With r = (2/M)(|U|^2 - T) on the window (0 elsewhere), the chain rule
+    gives dL/dphi = 2 Re(-i conj(x) [A^H (r U)]) restricted to the window.
+    """
+    phi = np.asarray(phi, dtype=np.float64)
+    h, w = phi.shape
+    oy, ox = offset
+    cy, cx = canvas
+    x = np.zeros((cy, cx), dtype=np.complex128)
+    x[oy:oy + h, ox:ox + w] = np.exp(1j * phi)
+    U = propagate(x, dx, dx, lam, z, ANGULAR)
+    Uw = U[oy:oy + h, ox:ox + w]
+    I_ = np.abs(Uw) ** 2
+    M = I_.size
+    diff = I_ - np.asarray(target, dtype=np.float64)
+    loss = float(np.sum(diff * diff) / M)
+    g = np.zeros((cy, cx), dtype=np.complex128)
+    g[oy:oy + h, ox:ox + w] = (2.0 / M) * diff * Uw
+    back = propagate(g, dx, dx, lam, z, ANGULAR, ADJOINT)
+    grad = 2.0 * np.real(-1j * np.conj(x[oy:oy + h, ox:ox + w]) * back[oy:oy + h, ox:ox + w])
+    return loss, grad

@@ -1,0 +1,270 @@
+"""Pins for the FP64 oracle: each check compares it with something other than itself --
+closed forms, special cases, invariants, brute force on tiny inputs, or physics that the
+paper's equations are derived from.  No GPU needed."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_5578_gb300 import synth
+
+LAM = 633e-9
+PITCH = 10e-6
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+# ------------------------------------------------------------------------------------- DFT/FFT
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 16])
+def test_dft_delta_gives_ones(n):
+    x = np.zeros(n, complex)
+    x[0] = 1.0
+    assert np.allclose(oracle.dft(x, -1), np.ones(n), atol=1e-14)
+
+
+@pytest.mark.parametrize("n,m", [(8, 1), (8, 3), (16, 5), (7, 2)])
+def test_dft_tone_gives_scaled_delta(n, m):
+    # forward sign -1: the tone exp(+2 pi i m j / n) lands on bin m with weight n
+    j = np.arange(n)
+    x = np.exp(2j * np.pi * m * j / n)
+    X = oracle.dft(x, -1)
+    want = np.zeros(n, complex)
+    want[m] = n
+    assert np.allclose(X, want, atol=1e-12)
+    # inverse sign +1 sends it to bin n - m
+    Xp = oracle.dft(x, +1)
+    want = np.zeros(n, complex)
+    want[(n - m) % n] = n
+    assert np.allclose(Xp, want, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32, 64])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fft_matches_direct_dft(n, sign):
+    x = synth.random_field(n, seed=n + (sign > 0), ny=1)[0]
+    assert rel(oracle.fft(x, sign), oracle.dft(x, sign)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [128, 1024, 4096])
+def test_fft_matches_numpy(n):
+    x = synth.random_field(n, seed=7, ny=1)[0]
+    assert rel(oracle.fft(x, -1), np.fft.fft(x)) < 1e-13
+    assert rel(oracle.fft(x, +1), np.fft.ifft(x) * n) < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(4, 8), (16, 16), (32, 8)])
+def test_fft2_matches_numpy(shape):
+    x = synth.random_field(shape[1], seed=3, ny=shape[0])
+    assert rel(oracle.fft2(x, -1), np.fft.fft2(x)) < 1e-13
+
+
+def test_fft_rejects_non_power_of_two():
+    with pytest.raises(ValueError):
+        oracle.fft(np.ones(12), -1)
+
+
+# ------------------------------------------------------------------- brute-force direct sums
+
+@pytest.mark.parametrize("nx,ny", [(8, 8), (16, 8), (4, 16)])
+@pytest.mark.parametrize("flags", [0, oracle.ADJOINT, oracle.LITERAL_SCALE])
+def test_fresnel_fft_equals_direct_sum(nx, ny, flags):
+    u = synth.random_field(nx, seed=11, ny=ny)
+    args = (PITCH, 1.5 * PITCH, LAM, 0.02)
+    a = oracle.propagate(u, *args, kind=oracle.FRESNEL_CONV, flags=flags)
+    b = oracle.propagate_direct(u, *args, kind=oracle.FRESNEL_CONV, flags=flags)
+    assert rel(a, b) < 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,dx,dy,z", [
+    (8, 8, 1e-6, 1e-6, 1e-4),        # several cycles of phase across the band
+    (16, 8, 1e-6, 2e-6, 3e-4),
+    (8, 4, 0.4e-6, 0.5e-6, 2e-6),    # pitch below lambda/sqrt(2): evanescent corners
+])
+@pytest.mark.parametrize("flags", [0, oracle.ADJOINT])
+def test_asm_fft_equals_kernel_sum(nx, ny, dx, dy, z, flags):
+    u = synth.random_field(nx, seed=5, ny=ny)
+    a = oracle.propagate(u, dx, dy, LAM, z, kind=oracle.ANGULAR, flags=flags)
+    b = oracle.propagate_direct(u, dx, dy, LAM, z, kind=oracle.ANGULAR, flags=flags)
+    assert rel(a, b) < 1e-12
+
+
+# --------------------------------------------------------------------- special cases / physics
+
+def test_asm_zero_distance_is_identity():
+    u = synth.random_field(64, seed=2, ny=32)
+    out = oracle.propagate(u, PITCH, PITCH, LAM, 0.0, kind=oracle.ANGULAR)
+    assert rel(out, u) < 1e-14
+
+
+@pytest.mark.parametrize("z", [0.05, 0.2, 1.0])
+def test_asm_normal_plane_wave_phase(z):
+    # a uniform field is the normally incident plane wave: it picks up exp(i k z), k = 2 pi / lambda
+    n = 16
+    u = np.ones((n, n), complex)
+    out = oracle.propagate(u, PITCH, PITCH, LAM, z, kind=oracle.ANGULAR, flags=oracle.NO_PAD)
+    want = np.exp(1j * 2 * np.pi * np.fmod(z / LAM, 1.0))
+    assert np.allclose(out, want, atol=1e-9)
+
+
+@pytest.mark.parametrize("a,b", [(1, 0), (3, -2), (-5, 7)])
+def test_asm_oblique_plane_wave_dispersion(a, b):
+    # exp(i (kx x + ky y)) is a Helmholtz solution that propagates as exp(i kz z) with
+    # kx^2 + ky^2 + kz^2 = k^2; on a circular grid it is an exact eigenvector of the method.
+    nx, ny, dx, dy, z = 32, 16, 2e-6, 3e-6, 4e-3
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    u = np.exp(2j * np.pi * (a * x / nx + b * y / ny))
+    kx, ky = 2 * np.pi * a / (nx * dx), 2 * np.pi * b / (ny * dy)
+    k = 2 * np.pi / LAM
+    kz = np.sqrt(k * k - kx * kx - ky * ky)
+    out = oracle.propagate(u, dx, dy, LAM, z, kind=oracle.ANGULAR, flags=oracle.NO_PAD)
+    assert np.allclose(out, np.exp(1j * kz * z) * u, atol=1e-9)
+
+
+def test_asm_evanescent_plane_wave_is_removed():
+    nx, dx = 16, 0.25e-6             # bin 7: |f| = 7/(16*0.25um) = 1.75/um > 1/lambda = 1.58/um
+    x = np.arange(nx)[None, :]
+    u = np.exp(2j * np.pi * 7 * x / nx) * np.ones((nx, 1))
+    out = oracle.propagate(u, dx, dx, LAM, 1e-6, kind=oracle.ANGULAR, flags=oracle.NO_PAD)
+    assert np.max(np.abs(out)) < 1e-13
+
+
+def test_asm_semigroup():
+    # on the circular grid A(z1 + z2) = A(z2) A(z1) exactly (products of exponentials)
+    u = synth.random_field(32, seed=9)
+    args = (1e-6, 1e-6, LAM)
+    ab = oracle.propagate(oracle.propagate(u, *args, 1e-4, flags=oracle.NO_PAD), *args, 2e-4,
+                          flags=oracle.NO_PAD)
+    c = oracle.propagate(u, *args, 3e-4, flags=oracle.NO_PAD)
+    assert rel(ab, c) < 1e-12
+
+
+def _fresnel_gaussian(r2, w0, z):
+    # closed-form Fresnel propagation of exp(-r^2/w0^2) (Gaussian integral of Eq. fre_conv)
+    alpha = LAM * z / (np.pi * w0 * w0)
+    return np.exp(1j * 2 * np.pi * np.fmod(z / LAM, 1.0)) / (1 + 1j * alpha) * \
+        np.exp(-r2 / (w0 * w0 * (1 + 1j * alpha)))
+
+
+def _grid_r2(n, pitch):
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    return ((x - n / 2) * pitch) ** 2 + ((y - n / 2) * pitch) ** 2
+
+
+def test_fresnel_gaussian_closed_form():
+    n, w0, z = 256, 200e-6, 0.1
+    u = synth.gaussian_beam(n, PITCH, w0)
+    out = oracle.propagate(u, PITCH, PITCH, LAM, z, kind=oracle.FRESNEL_CONV)
+    want = _fresnel_gaussian(_grid_r2(n, PITCH), w0, z)
+    assert np.max(np.abs(out - want)) < 1e-10
+    # the literal-scale reading differs by exactly the area element dx*dy
+    lit = oracle.propagate(u, PITCH, PITCH, LAM, z, kind=oracle.FRESNEL_CONV,
+                           flags=oracle.LITERAL_SCALE)
+    assert rel(lit * PITCH * PITCH, out) < 1e-13
+
+
+def test_asm_gaussian_matches_paraxial_closed_form():
+    # the exact (ASM) and paraxial (Fresnel) Gaussian differ by non-paraxial terms of order
+    # (z/lambda) * (lambda/(pi w0))^4 / 8 cycles ~ 1e-7 here
+    n, w0, z = 256, 200e-6, 0.1
+    u = synth.gaussian_beam(n, PITCH, w0)
+    out = oracle.propagate(u, PITCH, PITCH, LAM, z, kind=oracle.ANGULAR)
+    want = _fresnel_gaussian(_grid_r2(n, PITCH), w0, z)
+    err = np.max(np.abs(out - want))
+    assert 1e-10 < err < 2e-6
+
+
+def _hankel_asm_gaussian(r, w0, z, panels=400, nodes=24):
+    # u2(r) = 2 pi int_0^inf A(rho) H(rho) J0(2 pi rho r) rho d rho with the exact angular
+    # spectrum A(rho) = pi w0^2 exp(-pi^2 w0^2 rho^2) of exp(-r^2/w0^2)
+    from scipy.special import j0, roots_legendre
+    rho_max = np.sqrt(800.0) / (np.pi * w0)
+    xg, wg = roots_legendre(nodes)
+    edges = np.linspace(0.0, rho_max, panels + 1)
+    a, b = edges[:-1, None], edges[1:, None]
+    rho = (0.5 * (b - a) * xg[None, :] + 0.5 * (a + b)).ravel()
+    wt = (0.5 * (b - a) * wg[None, :]).ravel()
+    inv = 1.0 / LAM
+    # z (sqrt(1/lam^2 - rho^2) - 1/lam), written without cancellation
+    dphase = -z * rho * rho / (inv + np.sqrt(inv * inv - rho * rho))
+    A = np.pi * w0 * w0 * np.exp(-(np.pi * w0 * rho) ** 2)
+    integrand = A * np.exp(2j * np.pi * dphase) * rho * wt
+    out = 2 * np.pi * (j0(2 * np.pi * np.outer(r, rho)) @ integrand)
+    return np.exp(1j * 2 * np.pi * np.fmod(z / LAM, 1.0)) * out
+
+
+def test_asm_gaussian_hankel_quadrature():
+    n, w0, z = 256, 200e-6, 0.1
+    u = synth.gaussian_beam(n, PITCH, w0)
+    out = oracle.propagate(u, PITCH, PITCH, LAM, z, kind=oracle.ANGULAR)
+    cols = np.array([128, 130, 140, 150, 160, 180, 200])
+    r = (cols - n / 2) * PITCH
+    want = _hankel_asm_gaussian(r, w0, z)
+    assert np.max(np.abs(out[n // 2, cols] - want)) < 1e-10
+
+
+def test_asm_parseval_full_grid():
+    # with no evanescent bins |H| = 1, so the energy on the whole padded grid is conserved
+    u = synth.random_field(32, seed=4, ny=16)
+    out = oracle.propagate(u, PITCH, PITCH, LAM, 0.3, kind=oracle.ANGULAR,
+                           flags=oracle.FULL_OUTPUT)
+    assert out.shape == (32, 64)
+    e_in, e_out = np.sum(np.abs(u) ** 2), np.sum(np.abs(out) ** 2)
+    assert abs(e_out - e_in) / e_in < 1e-13
+
+
+def test_asm_z_then_minus_z_recovers_input():
+    # full padded grid forward by z, then back by -z on that circular grid: H(z) H(-z) = 1
+    u = synth.random_field(16, seed=8)
+    full = oracle.propagate(u, PITCH, PITCH, LAM, 0.05, flags=oracle.FULL_OUTPUT)
+    back = oracle.propagate(full, PITCH, PITCH, LAM, -0.05, flags=oracle.NO_PAD)
+    padded = np.zeros((32, 32), complex)
+    padded[:16, :16] = u
+    assert rel(back, padded) < 1e-13
+
+
+@pytest.mark.parametrize("kind", [oracle.ANGULAR, oracle.FRESNEL_CONV])
+def test_adjoint_dot_product(kind):
+    nx, ny = 32, 16
+    x = synth.random_field(nx, seed=21, ny=ny)
+    y = synth.random_field(nx, seed=22, ny=ny)
+    args = (2e-6, 3e-6, LAM, 2e-3)
+    Ax = oracle.propagate(x, *args, kind=kind)
+    AHy = oracle.propagate(y, *args, kind=kind, flags=oracle.ADJOINT)
+    lhs, rhs = np.vdot(y, Ax), np.vdot(AHy, x)
+    assert abs(lhs - rhs) / abs(lhs) < 1e-13
+
+
+def test_asm_adjoint_equals_back_propagation():
+    u = synth.random_field(16, seed=6)
+    a = oracle.propagate(u, PITCH, PITCH, LAM, 0.1, flags=oracle.ADJOINT)
+    b = oracle.propagate(u, PITCH, PITCH, LAM, -0.1)
+    assert rel(a, b) < 1e-13
+
+
+def test_hologram_gradient_central_differences():
+    g = synth.rng(31)
+    h, w, canvas, off = 12, 20, (32, 32), (10, 6)
+    phi = g.random((h, w)) * 2 * np.pi
+    tgt = g.random((h, w))
+    args = (canvas, off, tgt, 4e-6, 520e-9, 2e-3)
+    _, grad = oracle.hologram_loss_grad(phi, *args)
+    eps = 1e-5
+    for (i, j) in [(0, 0), (5, 7), (11, 19), (3, 12)]:
+        p, m = phi.copy(), phi.copy()
+        p[i, j] += eps
+        m[i, j] -= eps
+        fd = (oracle.hologram_loss_grad(p, *args)[0] - oracle.hologram_loss_grad(m, *args)[0]) / (2 * eps)
+        assert abs(fd - grad[i, j]) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_rejects_bad_arguments():
+    u = np.ones((8, 8), complex)
+    with pytest.raises(ValueError):
+        oracle.propagate(u, PITCH, PITCH, LAM, 0.0, kind=oracle.FRESNEL_CONV)
+    with pytest.raises(ValueError):
+        oracle.propagate(np.ones((8, 12), complex), PITCH, PITCH, LAM, 0.1)
+    with pytest.raises(ValueError):
+        oracle.propagate(u, -PITCH, PITCH, LAM, 0.1)
