@@ -1,0 +1,295 @@
+"""Benchmark: angular-spectrum propagation of 2048 x 2048 complex64 fields on GB300.
+
+One step = one batched call of the whole hot path (row forward FFT with fused zero padding,
+column FFT + transfer function + inverse column FFT, row inverse FFT with fused crop) over a
+batch of B synthetic 2048^2 fields resident in HBM (B * 32 MiB of input > L2, so no L2 flush is
+needed between steps).  Metric: propagations/s (whole job), plus HBM GB/s against the roofline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+
+Under torchrun each rank runs its own batch (independent items, no collective on the data
+path: weak scaling); the time is the max over ranks.  ``--impl reference`` times the FP64 CPU
+oracle on this host's cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 2048
+PITCH = 10e-6
+LAM = 633e-9
+Z = 0.05
+METRIC = "propagations/s (2048^2 angular spectrum, padded to 4096^2)"
+UNIT = "propagations/s"
+BYTES_PER_PROP = 80 * N * N          # 3 passes: 8N^2 + 16N^2 | 16N^2 + 16N^2 | 16N^2 + 8N^2
+COL_BYTES_PER_PROP = 32 * N * N      # column pass: read + write the Ny x Px intermediate
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1107_5578_gb300 import synth
+    oracle.build()
+    u = synth.random_field(N, seed=1)
+    oracle.propagate(u, PITCH, PITCH, LAM, Z, oracle.ANGULAR)   # warm page cache / threads
+    times = []
+    for _ in range(max(1, args.warmup)):
+        oracle.propagate(u, PITCH, PITCH, LAM, Z, oracle.ANGULAR)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.propagate(u, PITCH, PITCH, LAM, Z, oracle.ANGULAR)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    val = 1e3 / ms
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "asm_2048_pad4096", "n": N, "batch_per_step": 1,
+                                            "pitch_m": PITCH, "wavelength_m": LAM, "z_m": Z},
+            "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"1 propagation of one 2048^2 field per step, {args.steps} steps"},
+            "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """Oracle throughput on this host (bounded: one 2048^2 propagation, ~seconds)."""
+    import oracle
+    from paper_1107_5578_gb300 import synth
+    oracle.build()
+    u = synth.random_field(N, seed=1)
+    oracle.propagate(u, PITCH, PITCH, LAM, Z, oracle.ANGULAR)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.propagate(u, PITCH, PITCH, LAM, Z, oracle.ANGULAR)
+        reps += 1
+        if time.perf_counter() - t0 > 8.0 or reps >= 5:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": round(1.0 / dt, 4), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{reps} propagation(s) of one 2048^2 ASM field (FP64, OpenMP over rows/columns)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1107_5578_gb300 import cwo, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    B = args.batch
+    plan = cwo.Plan(N, N, PITCH, PITCH, LAM, Z, cwo.ANGULAR)
+    plan.reserve(B)
+    # synthetic inputs: B random fields per rank (amplitude U[0,1), phase U[0, 2 pi))
+    base = torch.from_numpy(synth.random_field(N, seed=1000 + rank).astype(np.complex64))
+    g = torch.Generator(device="cpu").manual_seed(rank)
+    host_in = torch.empty((B, N, N), dtype=torch.complex64).pin_memory()
+    for i in range(B):
+        host_in[i].copy_(base * torch.exp(1j * 2 * np.pi * torch.rand((), generator=g)).to(torch.complex64))
+    x = host_in.to(dev)
+    y = torch.empty_like(x)
+    host_out = torch.empty((B, N, N), dtype=torch.complex64).pin_memory()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing
+    for _ in range(args.warmup):
+        plan.propagate_batch(x, out=y)
+    barrier()
+    plan.set_timing_events(ev)
+    per_pass = np.zeros(3)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier()
+        t_start.record(stream)
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.propagate_batch(x, out=y)
+            # per-pass durations of this step (events recorded by the library on this stream)
+            ev[3].synchronize()
+            per_pass += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+        t_end.record(stream)
+        barrier()
+        wall1 = time.perf_counter()
+    plan.set_timing_events(None)
+    clocks = clk.summary()
+    ms_total = t_start.elapsed_time(t_end)
+    t = torch.tensor([ms_total], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    props = B * args.steps * world
+    value = props / (ms_total / 1e3)
+
+    # per-pass averages (ms per launch) and roofline of the dominant pass
+    pp = per_pass / args.steps
+    hbm_peak, sm_max, peak_kind = peaks()
+    names = ["row_fwd", "col_fwd_h_inv", "row_inv"]
+    dom = int(np.argmax(pp))
+    pass_bytes = [24 * N * N * B, 32 * N * N * B, 24 * N * N * B]
+    achieved = pass_bytes[dom] / (pp[dom] / 1e3) / 1e9
+    path_gbs = BYTES_PER_PROP * B / (sum(pp) / 1e3) / 1e9
+
+    # ---- end to end through the public API with host buffers
+    for _ in range(2):
+        x.copy_(host_in, non_blocking=True)
+        plan.propagate_batch(x, out=y)
+        host_out.copy_(y, non_blocking=True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e_steps = max(3, args.steps // 2)
+    e0.record(stream)
+    for _ in range(e_steps):
+        x.copy_(host_in, non_blocking=True)
+        plan.propagate_batch(x, out=y)
+        host_out.copy_(y, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e_ms = e0.elapsed_time(e1)
+    te = torch.tensor([e_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e_value = B * e_steps * world / (float(te.item()) / 1e3)
+
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline_sample()
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "asm_2048_pad4096", "n": N, "padded": 2 * N, "batch_per_step": B,
+                   "pitch_m": PITCH, "wavelength_m": LAM, "z_m": Z,
+                   "l2": "inputs larger than L2 (B x 32 MiB per step), no flush",
+                   "parallelism": f"independent items per rank x{world}"},
+        "hbm_gbs_path": round(path_gbs, 1),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                     "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                     "kernel": names[dom], "peak_kind": peak_kind},
+        "roofline_path": {"achieved": round(path_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                          "frac": round(path_gbs / hbm_peak, 4), "bytes_per_prop": BYTES_PER_PROP},
+        "passes_ms": {n: round(v, 4) for n, v in zip(names, pp)},
+        "clocks": clocks,
+        "e2e": {"value": round(e_value, 2), "unit": UNIT,
+                "h2d_bytes_per_step": B * N * N * 8, "d2h_bytes_per_step": B * N * N * 8},
+        "gpu_launches": plan.launches_per_call * args.steps,
+        "wall_s": round(wall1 - wall0, 3),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

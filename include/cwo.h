@@ -1,0 +1,164 @@
+/*
+ * cwo.h -- C ABI of libcwo_gb300.so: FFT-based scalar diffraction on one GB300 GPU.
+ *
+ * The library computes the two convolution-form diffraction methods of Shimobaba et al.,
+ * "Computational wave optics library for C++: CWO++ library":
+ *
+ *   CWO_ANGULAR       angular spectrum method (Section "Angular spectrum method", Eqs. ang1-ang3)
+ *                       u2 = IFFT[ FFT[u1] * H_A ],
+ *                       H_A(fx, fy) = exp(i z sqrt(k^2 - 4 pi^2 (fx^2 + fy^2))),  k = 2 pi / lambda
+ *   CWO_FRESNEL_CONV  Fresnel diffraction, convolution form (Section "Fresnel diffraction
+ *                     (convolution form)", Eqs. fre_conv, fre_conv_fft, fre_conv_prop_d)
+ *                       u2 = C * IFFT[ FFT[u1] * FFT[h_F] ],
+ *                       h_F(m, n) = exp(i pi ((m dx)^2 + (n dy)^2) / (lambda z)),
+ *                       C = dx dy exp(i 2 pi z / lambda) / (i lambda z)
+ *
+ * Every propagation zero-pads the Nx x Ny source to 2Nx x 2Ny (the source occupies the top-left
+ * block), transforms, multiplies by the transfer function, transforms back and keeps the exact
+ * Nx x Ny block (Section "Summary of diffraction calculation", Table "Classification of
+ * diffraction calculation").  The result equals the linear (not circular) convolution.
+ *
+ * Conventions the paper leaves open, as this library reads them:
+ *   - forward DFT unscaled with exp(-2 pi i k n / P); the inverse carries 1/(Px Py)
+ *   - frequency of bin k on the padded grid: f = kt / (P * pitch), kt = k for k < P/2, else k - P
+ *   - evanescent bins of H_A (negative radicand) are set to 0
+ *   - the Fresnel transfer function is the DFT of h_F sampled on the padded grid (index i maps
+ *     to displacement i for i < P/2, i - P otherwise); h_F is separable, so it is formed as the
+ *     outer product of two 1-D DFTs computed once per plan in double precision
+ *   - C includes the area element dx*dy of the discretised integral (CWO_FLAG_LITERAL_SCALE
+ *     drops it, which is the paper's printed coefficient)
+ *   - defaults (Section "CWO class", paragraph after Eq. norm): wavelength 633 nm, pitch 10 um;
+ *     pass CWO_DEFAULT_WAVELENGTH / CWO_DEFAULT_PITCH to use them
+ *
+ * Data layout: fields are complex64 (interleaved float re, im; torch.complex64), row-major
+ * [batch][Ny][Nx], contiguous, in DEVICE memory of the current CUDA device.  The caller owns all
+ * field buffers; input and output may alias (the input is fully consumed by the first pass before
+ * the output is written).  A plan owns its tables and its scratch (the 2N-wide intermediate).
+ *
+ * Precision: field and FFT arithmetic in FP32; the transfer-function phase (up to ~2e6 cycles for
+ * z / lambda at the studied sizes) is range-reduced in FP64 on per-axis tables, leaving an O(1)
+ * remainder that is evaluated per element in float-float / FP32 (see cwo_plan_create flags).
+ *
+ * Ordering: all work is enqueued on the caller's stream (a cudaStream_t passed as void*; NULL is
+ * the legacy default stream).  Calls do not synchronise the device, except cwo_plan_create and
+ * cwo_plan_reserve (allocation and the upload of the plan's tables).
+ *
+ * Errors: every entry point returns a cwo_status and never aborts.  Arguments are checked on the
+ * host before anything is enqueued; on failure nothing is launched.  cwo_last_error() returns a
+ * thread-local message describing the most recent failure on the calling thread.
+ *
+ * Thread safety: distinct plans may be used concurrently from different threads.  One plan must
+ * not be used by two threads at the same time, and calls on one plan that run concurrently on
+ * different streams race on the plan's scratch.
+ */
+#ifndef CWO_H
+#define CWO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CWO_DEFAULT_WAVELENGTH 633e-9
+#define CWO_DEFAULT_PITCH 10e-6
+#define CWO_MIN_SIDE 16
+#define CWO_MAX_SIDE 4096
+
+typedef enum {
+    CWO_ANGULAR = 0,          /* angular spectrum method (Eq. ang3)                      */
+    CWO_FRESNEL_CONV = 1,     /* Fresnel diffraction, convolution form (Eq. fre_conv_fft) */
+    CWO_FRESNEL_FOURIER = 2,  /* Fourier form (Eq. fre_fourier3): not provided, UNSUPPORTED */
+    CWO_SHIFTED_FRESNEL = 3,  /* shifted Fresnel: not provided, UNSUPPORTED               */
+    CWO_SHIFTED_ANGULAR = 4   /* shifted angular spectrum: not provided, UNSUPPORTED      */
+} cwo_type;
+
+typedef enum {
+    CWO_OK = 0,
+    CWO_ERR_INVALID_ARG = 1,  /* a size, pitch, wavelength, distance, pointer or flag is invalid */
+    CWO_ERR_UNSUPPORTED = 2,  /* a diffraction type or mode this library does not provide       */
+    CWO_ERR_OOM = 3,          /* device or pinned-host allocation failed                          */
+    CWO_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed                      */
+    CWO_ERR_TIMEOUT = 5       /* a bounded wait expired                                           */
+} cwo_status;
+
+/* plan flags */
+#define CWO_FLAG_PHASE_FP32    0x1u  /* precision study: evaluate the whole ASM phase in FP32   */
+#define CWO_FLAG_PHASE_FP64    0x2u  /* precision study: literal per-element FP64 ASM phase     */
+#define CWO_FLAG_LITERAL_SCALE 0x4u  /* Fresnel: C without the dx*dy area element              */
+
+typedef struct cwo_plan cwo_plan;
+
+/*
+ * Create a plan for Nx x Ny fields (each a power of two in [16, 4096]) with pitches dx, dy (> 0,
+ * metres), wavelength lambda (> 0, metres) and distance z (metres; any finite value for
+ * CWO_ANGULAR, z = 0 gives the identity; non-zero for CWO_FRESNEL_CONV).  The plan computes
+ * its per-axis tables in FP64 on the host ("once-calculation", Section "Performance") and uploads
+ * them, and allocates scratch for one field.  *out receives the plan; on failure *out is NULL.
+ */
+cwo_status cwo_plan_create(int nx, int ny, double dx, double dy, double lambda, double z,
+                           cwo_type type, unsigned flags, cwo_plan** out);
+
+/* Release a plan (NULL is accepted).  The caller must make sure no work using it is pending. */
+cwo_status cwo_plan_destroy(cwo_plan* plan);
+
+/* Device bytes a plan for this shape needs to run `batch` fields at once (tables + scratch),
+ * for admission control.  Host-only; touches no device. */
+cwo_status cwo_plan_device_bytes(int nx, int ny, int batch, size_t* bytes);
+
+/* Grow the plan's scratch so that batches of up to `batch` fields (or z-stacks of up to `batch`
+ * planes) run without allocating.  Synchronises the device when it reallocates. */
+cwo_status cwo_plan_reserve(cwo_plan* plan, int batch);
+
+/* One propagation of one [Ny][Nx] field with the plan's own parameters (Eq. ang3 or
+ * Eq. fre_conv_fft with the padding and crop above). */
+cwo_status cwo_propagate(cwo_plan* plan, const void* in_c64, void* out_c64, void* cuda_stream);
+
+/*
+ * Batched propagation of `batch` fields in one set of launches.
+ *   in_batch_stride  elements (complex64) between consecutive input fields; 0 means that every
+ *                    item propagates the SAME source field (3-D stack by stacking 2-D
+ *                    diffractions along z, Section "Three-dimensional diffraction calculations"):
+ *                    its spectrum is computed once and reused for every plane.
+ *   out              [batch][Ny][Nx]
+ *   z_or_null        NULL: every item uses the plan's z.  Otherwise a HOST array of `batch`
+ *                    distances; the per-item tables are computed in FP64 on the host and uploaded
+ *                    stream-ordered.
+ * Grows the scratch (synchronising) if `batch` exceeds the reserved size.
+ */
+cwo_status cwo_propagate_batch(cwo_plan* plan, const void* in, long long in_batch_stride,
+                               void* out, int batch, const double* z_or_null, void* cuda_stream);
+
+/* Adjoint propagation: the same passes with conj(H) (and conj(C)), i.e. the conjugate
+ * transpose of the linear map cwo_propagate applies; for CWO_ANGULAR without evanescent bins
+ * it equals back-propagation by -z (Section "Field type", back propagation of List
+ * lst:conversion). */
+cwo_status cwo_propagate_adjoint(cwo_plan* plan, const void* in_c64, void* out_c64, void* cuda_stream);
+
+/* Batched adjoint, same argument rules as cwo_propagate_batch (in_batch_stride must be > 0). */
+cwo_status cwo_propagate_adjoint_batch(cwo_plan* plan, const void* in, long long in_batch_stride,
+                                       void* out, int batch, const double* z_or_null,
+                                       void* cuda_stream);
+
+/* Number of kernel launches one call of cwo_propagate_batch makes for this plan (for launch
+ * accounting in benchmarks). */
+int cwo_launches_per_call(const cwo_plan* plan);
+
+/* Instrumentation: when `events` is non-NULL it must point to 4 cudaEvent_t (passed as void*)
+ * created by the caller on the plan's device; every later call records events[0] before the row
+ * forward pass, events[1] after it, events[2] after the column pass and events[3] after the row
+ * inverse pass, on the call's stream, so that per-pass durations can be read with
+ * cudaEventElapsedTime.  NULL switches recording off.  The caller keeps ownership of the events. */
+cwo_status cwo_plan_set_timing_events(cwo_plan* plan, void* const* events);
+
+/* Thread-local description of the most recent failure on this thread ("" if none). */
+const char* cwo_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int cwo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CWO_H */

@@ -1,0 +1,55 @@
+/*
+ * cwo_debug.h -- host-only diagnostic entry points of libcwo_gb300.so.
+ *
+ * They expose the FP64 host computations the plans are built from, so that tests can check them
+ * on a machine without a GPU.  None of them touches a device.  They return CWO_ERR_INVALID_ARG on
+ * bad arguments (message in cwo_last_error()).
+ */
+#ifndef CWO_DEBUG_H
+#define CWO_DEBUG_H
+
+#include "cwo.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Axis index -> frequency bin (0 .. p-1) for a padded axis of length p (power of two in
+ * [32, 8192]).  Index idx = e*(p/16) + t is register e of thread t in the last forward FFT stage,
+ * which holds the output at digit-reversed (DIF) position 16 t + e; along x the same index is
+ * the storage column of the 2Nx-wide intermediate.  bins: p ints, caller-owned. */
+cwo_status cwo_debug_axis_bins(int p, int* bins);
+
+/* The length-p DFT (forward sign, unscaled) of the Fresnel impulse response sampled on the
+ * padded axis, h(d) = exp(i pi (d pitch)^2 / (lambda z)), d = i for i < p/2 else i - p
+ * (Eq. fre_conv_prop_d, one separable factor), in natural bin order, FP64.
+ * out_ri: 2p doubles (re, im interleaved), caller-owned. */
+cwo_status cwo_debug_fresnel_axis(int p, double pitch, double lambda, double z, double* out_ri);
+
+/* Inter-stage twiddle table of an axis of length p: (stages-1) blocks of p complex64 values,
+ * block s holding W_{L_s}^{(t mod S_s) k} at [k][t].  out_ri: 2 * (stages-1) * p floats. */
+cwo_status cwo_debug_twiddles(int p, float* out_ri);
+
+/* ASM per-axis table {a, W - c0, u_hi, u_lo} of an axis of length p (see cwo_cols.cu) in axis
+ * index order.  is_x selects the x-axis variant (frac(z/lambda) and the sign of z folded in).
+ * out4: 4p floats. */
+cwo_status cwo_debug_asm_axis(int p, double pitch, double lambda, double z, int is_x, float* out4);
+
+/* Host emulation of the three CUDA passes for one [ny][nx] complex64 field (same butterflies,
+ * stage positions, tables and transfer-function code, executed serially on the CPU).  type is
+ * CWO_ANGULAR or CWO_FRESNEL_CONV, flags 0 or CWO_FLAG_LITERAL_SCALE, adjoint 0/1.  in_ri and
+ * out_ri: 2 nx ny floats each, caller-owned host memory.  Slow; meant for small fields. */
+cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, double lambda, double z,
+                             int type, unsigned flags, int adjoint, const float* in_ri, float* out_ri);
+
+/* Host emulation of one padded line transform of length p.  inverse = 0: forward transform of
+ * p/2 natural-order samples (the upper half is the zero padding) into p values in axis-index
+ * order.  inverse = 1: adjoint of p axis-index-order values, returning the first p/2 natural-order
+ * outputs (unscaled). */
+cwo_status cwo_debug_line_fft(int p, int inverse, const float* in_ri, float* out_ri);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CWO_DEBUG_H */

@@ -1,0 +1,162 @@
+// cwo_emu.cpp -- host emulation of the three CUDA passes (test support).
+//
+// Runs the same butterflies, stage positions, twiddle tables, transfer-function code and table
+// generation as the kernels, one "thread" at a time, with a plain array standing in for shared
+// memory.  It lets the host-only test suite check the FFT index logic against the oracle on a
+// machine without a GPU.  It is slow and only meant for small fields.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "../../include/cwo.h"
+#include "../../include/cwo_debug.h"
+#include "cwo_fft.cuh"
+#include "cwo_h.cuh"
+#include "cwo_tables.h"
+
+namespace cwo {
+namespace {
+
+struct Regs { float2 v[16]; };
+
+template <int P, int S, bool INV>
+void emu_twiddle(std::vector<Regs>& R, const float2* tw) {
+    constexpr int T = Geo<P>::T;
+    for (int t = 0; t < T; ++t)
+        for (int k = 1; k < 16; ++k) {
+            const float2 w = tw[S * P + k * T + t];
+            R[t].v[k] = INV ? cmulc(R[t].v[k], w) : cmul(R[t].v[k], w);
+        }
+}
+
+template <int P, int SW, int SR>
+void emu_exchange(std::vector<Regs>& R) {
+    constexpr int T = Geo<P>::T;
+    std::vector<float2> sm(P);
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < 16; ++e) sm[swz<P, 1>(0, stage_pos<P, SW>(t, e))] = R[t].v[e];
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < 16; ++e) R[t].v[e] = sm[swz<P, 1>(0, stage_pos<P, SR>(t, e))];
+}
+
+template <int P, int S, int NZ0>
+void emu_fwd_from(std::vector<Regs>& R, const float2* tw) {
+    using G = Geo<P>;
+    for (int t = 0; t < G::T; ++t) stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(R[t].v);
+    if constexpr (S < G::NST - 1) {
+        emu_twiddle<P, S, false>(R, tw);
+        emu_exchange<P, S, S + 1>(R);
+        emu_fwd_from<P, S + 1, NZ0>(R, tw);
+    }
+}
+
+template <int P, int S>
+void emu_inv_from(std::vector<Regs>& R, const float2* tw) {
+    using G = Geo<P>;
+    if constexpr (S < G::NST - 1) emu_twiddle<P, S, true>(R, tw);
+    for (int t = 0; t < G::T; ++t) stage_butterflies<P, S, true, 16>(R[t].v);
+    if constexpr (S > 0) {
+        emu_exchange<P, S, S - 1>(R);
+        emu_inv_from<P, S - 1>(R, tw);
+    }
+}
+
+// forward transform of one padded line: in[0..P/2) nonzero; out in axis-index order
+template <int P>
+void emu_line_fwd(const float2* in, long long in_step, float2* out, long long out_step, const float2* tw) {
+    constexpr int T = P / 16;
+    std::vector<Regs> R(T);
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < 16; ++e)
+            R[t].v[e] = e < 8 ? in[(long long)(t + e * T) * in_step] : make_float2(0.f, 0.f);
+    emu_fwd_from<P, 0, 8>(R, tw);
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < 16; ++e) out[(long long)(e * T + t) * out_step] = R[t].v[e];
+}
+
+// adjoint transform of one line given in axis-index order; keeps the first P/2 outputs
+template <int P>
+void emu_line_inv(const float2* in, long long in_step, float2* out, long long out_step, const float2* tw) {
+    constexpr int T = P / 16;
+    std::vector<Regs> R(T);
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < 16; ++e) R[t].v[e] = in[(long long)(e * T + t) * in_step];
+    emu_inv_from<P, Geo<P>::NST - 1>(R, tw);
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < 8; ++e) out[(long long)(t + e * T) * out_step] = R[t].v[e];
+}
+
+using LineFn = void (*)(const float2*, long long, float2*, long long, const float2*);
+
+LineFn pick_fwd(int p) {
+    switch (p) {
+        case 32: return emu_line_fwd<32>; case 64: return emu_line_fwd<64>; case 128: return emu_line_fwd<128>;
+        case 256: return emu_line_fwd<256>; case 512: return emu_line_fwd<512>; case 1024: return emu_line_fwd<1024>;
+        case 2048: return emu_line_fwd<2048>; case 4096: return emu_line_fwd<4096>; case 8192: return emu_line_fwd<8192>;
+        default: return nullptr;
+    }
+}
+LineFn pick_inv(int p) {
+    switch (p) {
+        case 32: return emu_line_inv<32>; case 64: return emu_line_inv<64>; case 128: return emu_line_inv<128>;
+        case 256: return emu_line_inv<256>; case 512: return emu_line_inv<512>; case 1024: return emu_line_inv<1024>;
+        case 2048: return emu_line_inv<2048>; case 4096: return emu_line_inv<4096>; case 8192: return emu_line_inv<8192>;
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+}  // namespace cwo
+
+extern "C" cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, double lambda, double z,
+                                        int type, unsigned flags, int adjoint, const float* in_ri,
+                                        float* out_ri) {
+    using namespace cwo;
+    using namespace cwo::host;
+    if (!in_ri || !out_ri || nx < 16 || ny < 16 || nx > 4096 || ny > 4096 || (nx & (nx - 1)) || (ny & (ny - 1)) ||
+        !(dx > 0) || !(dy > 0) || !(lambda > 0) || (type != CWO_ANGULAR && type != CWO_FRESNEL_CONV) ||
+        (type == CWO_FRESNEL_CONV && z == 0.0) || (flags & ~CWO_FLAG_LITERAL_SCALE))
+        return CWO_ERR_INVALID_ARG;
+    const int px = 2 * nx, py = 2 * ny;
+    const AxisGeo gx(px), gy(py);
+    const std::vector<float2> twx = twiddle_table(gx), twy = twiddle_table(gy);
+    std::vector<float4> ax(px), ay(py);
+    std::vector<float2> hx(px), hy(py);
+    float K = 0.f;
+    const bool fresnel = type == CWO_FRESNEL_CONV;
+    make_h_tables(px, py, dx, dy, lambda, z, fresnel, (flags & CWO_FLAG_LITERAL_SCALE) != 0,
+                  ax.data(), ay.data(), hx.data(), hy.data(), &K);
+    const float2* in = (const float2*)in_ri;
+    float2* out = (float2*)out_ri;
+    std::vector<float2> W((size_t)ny * px);
+    LineFn fx = pick_fwd(px), ix = pick_inv(px), fy = pick_fwd(py), iy = pick_inv(py);
+    for (int y = 0; y < ny; ++y) fx(in + (size_t)y * nx, 1, W.data() + (size_t)y * px, 1, twx.data());
+    std::vector<float2> col(py);
+    for (int c = 0; c < px; ++c) {
+        fy(W.data() + c, px, col.data(), 1, twy.data());
+        for (int i = 0; i < py; ++i) {
+            float2 h = fresnel ? cmul(hx[c], hy[i]) : asm_h_reduced(ax[c], ay[i], K);
+            col[i] = adjoint ? cmulc(col[i], h) : cmul(col[i], h);
+        }
+        iy(col.data(), 1, W.data() + c, px, twy.data());
+    }
+    const float scale = (float)(1.0 / ((double)px * (double)py));
+    std::vector<float2> line(nx);
+    for (int y = 0; y < ny; ++y) {
+        ix(W.data() + (size_t)y * px, 1, line.data(), 1, twx.data());
+        for (int x = 0; x < nx; ++x) out[(size_t)y * nx + x] = cscale(line[x], scale);
+    }
+    return CWO_OK;
+}
+
+extern "C" cwo_status cwo_debug_line_fft(int p, int inverse, const float* in_ri, float* out_ri) {
+    using namespace cwo;
+    using namespace cwo::host;
+    if (!in_ri || !out_ri || p < 32 || p > 8192 || (p & (p - 1))) return CWO_ERR_INVALID_ARG;
+    const AxisGeo g(p);
+    const std::vector<float2> tw = twiddle_table(g);
+    if (!inverse) pick_fwd(p)((const float2*)in_ri, 1, (float2*)out_ri, 1, tw.data());
+    else pick_inv(p)((const float2*)in_ri, 1, (float2*)out_ri, 1, tw.data());
+    return CWO_OK;
+}

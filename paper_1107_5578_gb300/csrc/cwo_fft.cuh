@@ -1,0 +1,245 @@
+// cwo_fft.cuh -- device building blocks of the register/shared-memory FFT used by all passes.
+//
+// A length-P transform (P = 2^p, 32 <= P <= 8192) is computed by T = P/16 threads that each hold
+// 16 complex64 values in registers.  The forward transform is an in-place mixed-radix
+// decimation-in-frequency (DIF) FFT: stages 0 .. NST-2 have radix 16, the last stage has radix
+// RLAST in {2, 4, 8, 16}.  No digit-reversal pass is made: the forward output stays in DIF
+// (digit-reversed) order, the transfer function is applied in that order, and the inverse is the
+// exact adjoint of the forward stages (conjugate twiddles, inverse butterflies, stages in reverse),
+// which consumes digit-reversed input and returns natural order.  Between stages the values are
+// exchanged through shared memory with an XOR swizzle that keeps every access bank-conflict free.
+//
+// Stage s works on sub-transforms of length L_s = P / 16^s with stride S_s = L_s / radix(s).
+//   stage s < NST-1 : thread t owns butterfly t: block b = t / S_s, offset j = t % S_s, and its
+//                     register e holds position b L_s + j + e S_s; after the radix-16 DFT,
+//                     output k' is multiplied by W_{L_s}^{j k'}, W_L = exp(-2 pi i / L).
+//   stage NST-1     : thread t owns positions 16 t + e (consecutive butterflies of radix RLAST).
+// The DIF position of frequency k = sum_s k_s prod_{i<s} r_i is sum_s k_s P / prod_{i<=s} r_i.
+//
+// These are the FFT steps of Eqs. ang3 and fre_conv_fft (FFT / IFFT), restated for sm_103a.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define CWO_HD __host__ __device__ __forceinline__
+
+namespace cwo {
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+template <int P>
+struct Geo {
+    static constexpr int LOG = ilog2c(P);
+    static constexpr int NST = (LOG + 3) / 4;
+    static constexpr int RLAST = 1 << (LOG - 4 * (NST - 1));
+    static constexpr int T = P / 16;
+    static __host__ __device__ constexpr int radix(int s) { return s == NST - 1 ? RLAST : 16; }
+    static __host__ __device__ constexpr int len(int s) { return P >> (4 * s); }
+    static __host__ __device__ constexpr int stride(int s) { return len(s) / radix(s); }
+    static_assert(P >= 32 && P <= 8192 && (P & (P - 1)) == 0, "P must be a power of two in [32, 8192]");
+};
+
+// ------------------------------------------------------------------------------- complex helpers
+CWO_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+CWO_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+CWO_HD float2 cmul(float2 a, float2 w) {
+    return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+CWO_HD float2 cmulc(float2 a, float2 w) {  // a * conj(w)
+    return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
+}
+CWO_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// multiply by W_4 = -i (forward) or +i (inverse)
+template <bool INV> CWO_HD float2 mul_w4(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+constexpr float kRsqrt2 = 0.70710678118654752440f;
+constexpr float kCos1 = 0.92387953251128675613f;  // cos(pi/8)
+constexpr float kSin1 = 0.38268343236508977173f;  // sin(pi/8)
+
+// multiply by W_16^E (E = 0..9), W_16 = exp(-+ 2 pi i / 16) for forward / inverse
+template <bool INV, int E> CWO_HD float2 mul_w16(float2 a) {
+    constexpr float sg = INV ? 1.0f : -1.0f;
+    if constexpr (E == 0) return a;
+    else if constexpr (E == 4) return mul_w4<INV>(a);
+    else if constexpr (E == 8) return make_float2(-a.x, -a.y);
+    else if constexpr (E == 2) {  // (1 -+ i)/sqrt2
+        return INV ? make_float2((a.x - a.y) * kRsqrt2, (a.x + a.y) * kRsqrt2)
+                   : make_float2((a.x + a.y) * kRsqrt2, (a.y - a.x) * kRsqrt2);
+    } else if constexpr (E == 6) {  // (-1 -+ i)/sqrt2
+        return INV ? make_float2(-(a.x + a.y) * kRsqrt2, (a.x - a.y) * kRsqrt2)
+                   : make_float2((a.y - a.x) * kRsqrt2, -(a.x + a.y) * kRsqrt2);
+    } else if constexpr (E == 1) {
+        return cmul(a, make_float2(kCos1, sg * kSin1));
+    } else if constexpr (E == 3) {
+        return cmul(a, make_float2(kSin1, sg * kCos1));
+    } else if constexpr (E == 9) {
+        return cmul(a, make_float2(-kCos1, -sg * kSin1));
+    } else {
+        static_assert(E < 0, "unused exponent");
+        return a;
+    }
+}
+
+// ----------------------------------------------------------------------------- small DFTs
+// All operate in place on v[B .. B+R) with natural-order input and output.
+template <bool INV, int B, int ST = 1>
+CWO_HD void dft4(float2 (&v)[16]) {
+    float2 a0 = v[B], a1 = v[B + ST], a2 = v[B + 2 * ST], a3 = v[B + 3 * ST];
+    float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_w4<INV>(csub(a1, a3));
+    v[B] = cadd(t0, t2);
+    v[B + ST] = cadd(t1, t3);
+    v[B + 2 * ST] = csub(t0, t2);
+    v[B + 3 * ST] = csub(t1, t3);
+}
+// radix-4 whose last two inputs are zero
+template <bool INV, int B, int ST = 1>
+CWO_HD void dft4_half(float2 (&v)[16]) {
+    float2 a0 = v[B], a1 = v[B + ST];
+    float2 r = mul_w4<INV>(a1);
+    v[B] = cadd(a0, a1);
+    v[B + ST] = cadd(a0, r);
+    v[B + 2 * ST] = csub(a0, a1);
+    v[B + 3 * ST] = csub(a0, r);
+}
+
+template <bool INV, int B>
+CWO_HD void dft2(float2 (&v)[16]) {
+    float2 a = v[B], b = v[B + 1];
+    v[B] = cadd(a, b);
+    v[B + 1] = csub(a, b);
+}
+
+template <bool INV, int B>
+CWO_HD void dft8(float2 (&v)[16]) {
+    float2 e0 = v[B], e1 = v[B + 2], e2 = v[B + 4], e3 = v[B + 6];
+    float2 o0 = v[B + 1], o1 = v[B + 3], o2 = v[B + 5], o3 = v[B + 7];
+    {   // even and odd radix-4 DFTs
+        float2 t0 = cadd(e0, e2), t1 = csub(e0, e2), t2 = cadd(e1, e3), t3 = mul_w4<INV>(csub(e1, e3));
+        e0 = cadd(t0, t2); e1 = cadd(t1, t3); e2 = csub(t0, t2); e3 = csub(t1, t3);
+        float2 s0 = cadd(o0, o2), s1 = csub(o0, o2), s2 = cadd(o1, o3), s3 = mul_w4<INV>(csub(o1, o3));
+        o0 = cadd(s0, s2); o1 = cadd(s1, s3); o2 = csub(s0, s2); o3 = csub(s1, s3);
+    }
+    o1 = mul_w16<INV, 2>(o1);
+    o2 = mul_w4<INV>(o2);
+    o3 = mul_w16<INV, 6>(o3);
+    v[B] = cadd(e0, o0); v[B + 4] = csub(e0, o0);
+    v[B + 1] = cadd(e1, o1); v[B + 5] = csub(e1, o1);
+    v[B + 2] = cadd(e2, o2); v[B + 6] = csub(e2, o2);
+    v[B + 3] = cadd(e3, o3); v[B + 7] = csub(e3, o3);
+}
+
+// 16-point DFT as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.  NZ = 8: inputs 8..15 are zero.
+template <bool INV, int NZ>
+CWO_HD void dft16(float2 (&v)[16]) {
+    if constexpr (NZ == 8) {
+        dft4_half<INV, 0, 4>(v); dft4_half<INV, 1, 4>(v); dft4_half<INV, 2, 4>(v); dft4_half<INV, 3, 4>(v);
+    } else {
+        dft4<INV, 0, 4>(v); dft4<INV, 1, 4>(v); dft4<INV, 2, 4>(v); dft4<INV, 3, 4>(v);
+    }
+    // v[n2 + 4 k1] *= W16^(n2 k1)
+    v[5] = mul_w16<INV, 1>(v[5]);   v[6] = mul_w16<INV, 2>(v[6]);   v[7] = mul_w16<INV, 3>(v[7]);
+    v[9] = mul_w16<INV, 2>(v[9]);   v[10] = mul_w16<INV, 4>(v[10]); v[11] = mul_w16<INV, 6>(v[11]);
+    v[13] = mul_w16<INV, 3>(v[13]); v[14] = mul_w16<INV, 6>(v[14]); v[15] = mul_w16<INV, 9>(v[15]);
+    dft4<INV, 0, 1>(v); dft4<INV, 4, 1>(v); dft4<INV, 8, 1>(v); dft4<INV, 12, 1>(v);
+    // X[k1 + 4 k2] sits in v[4 k1 + k2]: transpose the 4 x 4 register block
+    float2 w[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w[i] = v[i];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = w[4 * k1 + k2];
+}
+
+// the butterflies of stage S on a thread's 16 registers
+template <int P, int S, bool INV, int NZ>
+CWO_HD void stage_butterflies(float2 (&v)[16]) {
+    constexpr int R = Geo<P>::radix(S);
+    if constexpr (R == 16) {
+        dft16<INV, NZ>(v);
+    } else if constexpr (R == 8) {
+        dft8<INV, 0>(v); dft8<INV, 8>(v);
+    } else if constexpr (R == 4) {
+        dft4<INV, 0>(v); dft4<INV, 4>(v); dft4<INV, 8>(v); dft4<INV, 12>(v);
+    } else {
+        static_assert(R == 2, "radix");
+        dft2<INV, 0>(v); dft2<INV, 2>(v); dft2<INV, 4>(v); dft2<INV, 6>(v);
+        dft2<INV, 8>(v); dft2<INV, 10>(v); dft2<INV, 12>(v); dft2<INV, 14>(v);
+    }
+}
+
+// position held by register e of thread t at stage S
+template <int P, int S>
+CWO_HD int stage_pos(int t, int e) {
+    using G = Geo<P>;
+    if constexpr (S == G::NST - 1) {
+        return 16 * t + e;
+    } else {
+        constexpr int L = G::len(S), St = G::stride(S);
+        return (t / St) * L + (t % St) + e * St;
+    }
+}
+
+// shared-memory word of position pos of transform c (C transforms per block)
+template <int P, int C>
+CWO_HD int swz(int c, int pos) {
+    constexpr int K = C >= 16 ? 1 : 16 / C;
+    return c * P + (pos ^ (((pos >> 4) ^ (c * K)) & 15));
+}
+
+#ifdef __CUDACC__
+// write the registers at the positions of stage SW, read them back at the positions of stage SR
+template <int P, int C, int SW, int SR>
+__device__ __forceinline__ void exchange(float2* __restrict__ sm, int c, int t, float2 (&v)[16]) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) sm[swz<P, C>(c, stage_pos<P, SW>(t, e))] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = sm[swz<P, C>(c, stage_pos<P, SR>(t, e))];
+    __syncthreads();
+}
+
+// inter-stage twiddles of stage S (< NST-1): table block S holds W_{L_S}^{(t % S_S) k'} at [k'][t]
+template <int P, int S, bool INV>
+__device__ __forceinline__ void stage_twiddle(float2 (&v)[16], int t, const float2* __restrict__ tw) {
+    constexpr int T = Geo<P>::T;
+    const float2* base = tw + S * P + t;
+#pragma unroll
+    for (int k = 1; k < 16; ++k) {
+        float2 w = __ldg(base + k * T);
+        v[k] = INV ? cmulc(v[k], w) : cmul(v[k], w);
+    }
+}
+
+// forward DIF from stage S to the end; the registers enter holding stage-S input positions
+template <int P, int C, int S, int NZ0>
+__device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ sm, int c, int t,
+                                         const float2* __restrict__ tw) {
+    using G = Geo<P>;
+    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(v);
+    if constexpr (S < G::NST - 1) {
+        stage_twiddle<P, S, false>(v, t, tw);
+        exchange<P, C, S, S + 1>(sm, c, t, v);
+        fwd_from<P, C, S + 1, NZ0>(v, sm, c, t, tw);
+    }
+}
+
+// adjoint (inverse DIT) from stage S down to stage 0; the registers enter holding stage-S positions
+template <int P, int C, int S>
+__device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ sm, int c, int t,
+                                         const float2* __restrict__ tw) {
+    using G = Geo<P>;
+    if constexpr (S < G::NST - 1) stage_twiddle<P, S, true>(v, t, tw);
+    stage_butterflies<P, S, true, 16>(v);
+    if constexpr (S > 0) {
+        exchange<P, C, S, S - 1>(sm, c, t, v);
+        inv_from<P, C, S - 1>(v, sm, c, t, tw);
+    }
+}
+
+#endif  // __CUDACC__
+
+}  // namespace cwo

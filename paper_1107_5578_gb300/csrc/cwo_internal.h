@@ -1,0 +1,52 @@
+// cwo_internal.h -- structures shared by the host plan code and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace cwo {
+
+enum HMode : int {
+    HMODE_ASM_REDUCED = 0,   // ASM, FP64-reduced per-axis phase + float-float cross term
+    HMODE_ASM_FP32 = 1,      // ASM, whole phase in FP32 (precision-study arm)
+    HMODE_ASM_FP64 = 2,      // ASM, literal per-element FP64 phase (precision-study arm)
+    HMODE_FRESNEL = 3,       // Fresnel, separable table product
+};
+
+// Transfer-function description for the column pass.  Per-axis tables are indexed by the axis
+// index idx = e * T + t (register e of thread t in the last forward stage, i.e. DIF position
+// 16 t + e); along x the same index is the storage column of the intermediate.
+struct HParams {
+    int mode;                 // HMode
+    int conj;                 // 1: adjoint (conj H)
+    // ASM reduced: float4 {a = lambda^2 f^2, W = frac(K(a/2 + a^2/8)) [- frac(K) on x], u_hi, u_lo}
+    // with K = z / lambda and u_hi + u_lo = sqrt(K/4) a; K is folded into the tables.
+    const float4* ax;
+    const float4* ay;
+    // Fresnel: float2 per-axis DFTs of the sampled chirp (x table includes C)
+    const float2* hx;
+    const float2* hy;
+    long long x_item_stride;  // elements between items' x tables (0: shared)
+    long long y_item_stride;
+    const float* kf;          // ASM reduced: K = z / lambda per item (for the O(s^3) tail term)
+    long long kf_item_stride; // 0: shared
+    double K;                 // z / lambda                       (FP64 arm)
+    double sx, sy;            // lambda^2 / (P dx)^2, (P dy)^2    (FP64 arm)
+    double z, k;              // distance and wavenumber 2 pi / lambda   (FP32 arm)
+    double dfx, dfy;          // frequency pitches 1 / (P dx), 1 / (P dy) (FP32 arm)
+    const int* kbx;           // signed bin of each axis index (FP32 / FP64 arms)
+    const int* kby;
+};
+
+// launchers (return cudaGetLastError() after the launch)
+cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, float2* w,
+                           long long w_item_stride, int ny, int items, const float2* tw,
+                           cudaStream_t st);
+cudaError_t launch_row_inv(int px, const float2* w, long long w_item_stride, float2* out,
+                           long long out_item_stride, int ny, int items, float scale,
+                           const float2* tw, cudaStream_t st);
+cudaError_t launch_col(int py, const float2* win, long long win_item_stride, float2* wout,
+                       long long wout_item_stride, int px, int items, const float2* tw,
+                       const HParams& hp, cudaStream_t st);
+
+}  // namespace cwo

@@ -1,0 +1,498 @@
+// cwo_plan.cpp -- host side of libcwo_gb300: plans, FP64 per-axis tables, argument checking,
+// scratch management and the C ABI declared in include/cwo.h.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cwo.h"
+#include "../../include/cwo_debug.h"
+#include "cwo_internal.h"
+#include "cwo_tables.h"
+
+using cd = std::complex<double>;
+using namespace cwo::host;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+thread_local std::string g_err;
+
+cwo_status fail(cwo_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+cwo_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(CWO_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool pow2_side(int n) { return n >= CWO_MIN_SIDE && n <= CWO_MAX_SIDE && (n & (n - 1)) == 0; }
+
+// ------------------------------------------------------------------------------------------
+// driver entry point for allocation-range checks (avoids a link-time dependency on libcuda)
+// ------------------------------------------------------------------------------------------
+typedef CUresult (*PFN_memGetAddressRange)(CUdeviceptr*, size_t*, CUdeviceptr);
+PFN_memGetAddressRange get_addr_range_fn() {
+    static PFN_memGetAddressRange fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_memGetAddressRange)p;
+    });
+    return fn;
+}
+
+// Check that [ptr, ptr + bytes) is device memory of `device` inside one allocation.
+cwo_status check_device_range(const void* ptr, size_t bytes, int device, const char* name) {
+    if (!ptr) return fail(CWO_ERR_INVALID_ARG, "%s is NULL", name);
+    if ((uintptr_t)ptr % 8 != 0) return fail(CWO_ERR_INVALID_ARG, "%s is not 8-byte aligned", name);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CWO_ERR_INVALID_ARG, "%s: not a CUDA pointer (%s)", name, cudaGetErrorName(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(CWO_ERR_INVALID_ARG, "%s is not device memory", name);
+    if (at.type == cudaMemoryTypeDevice && at.device != device)
+        return fail(CWO_ERR_INVALID_ARG, "%s lives on device %d, the plan on device %d", name, at.device, device);
+    if (PFN_memGetAddressRange fn = get_addr_range_fn()) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (fn(&base, &size, (CUdeviceptr)(uintptr_t)ptr) == CUDA_SUCCESS) {
+            if ((uintptr_t)ptr + bytes > (uintptr_t)base + size)
+                return fail(CWO_ERR_INVALID_ARG, "%s: %zu bytes requested but its allocation ends %zu bytes after it",
+                            name, bytes, (size_t)((uintptr_t)base + size - (uintptr_t)ptr));
+        }
+    }
+    return CWO_OK;
+}
+
+template <typename T>
+cwo_status dev_alloc(T** p, size_t count, const char* what) {
+    *p = nullptr;
+    if (count == 0) return CWO_OK;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(CWO_ERR_OOM, "cudaMalloc of %zu bytes for %s failed: %s", count * sizeof(T), what, cudaGetErrorName(e));
+    }
+    return CWO_OK;
+}
+
+template <typename T>
+cwo_status upload(T* dst, const std::vector<T>& src, const char* what) {
+    if (src.empty()) return CWO_OK;
+    cudaError_t e = cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? CWO_OK : cuda_fail(e, what);
+}
+
+size_t tables_bytes(int nx, int ny) {
+    const AxisGeo gx(2 * nx), gy(2 * ny);
+    size_t b = 0;
+    b += (size_t)std::max(gx.NST - 1, 0) * gx.P * sizeof(float2) + (size_t)std::max(gy.NST - 1, 0) * gy.P * sizeof(float2);
+    b += (size_t)(gx.P + gy.P) * sizeof(int);
+    b += (size_t)(gx.P + gy.P) * sizeof(float4) + sizeof(float) * 2;
+    return b;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// plan
+// ------------------------------------------------------------------------------------------
+struct cwo_plan {
+    int nx = 0, ny = 0, px = 0, py = 0;
+    double dx = 0, dy = 0, lambda = 0, z = 0;
+    cwo_type type = CWO_ANGULAR;
+    unsigned flags = 0;
+    int device = 0;
+    float2* tw_x = nullptr;   // twiddles along x (rows, length px)
+    float2* tw_y = nullptr;   // twiddles along y (columns, length py); aliases tw_x if px == py
+    int* kb_x = nullptr;
+    int* kb_y = nullptr;
+    // tables of the plan's own z
+    float4* ax = nullptr; float4* ay = nullptr;
+    float2* hx = nullptr; float2* hy = nullptr;
+    float* kf = nullptr;
+    // per-call (per-item z) tables
+    int zcap = 0;
+    float4* zax = nullptr; float4* zay = nullptr;
+    float2* zhx = nullptr; float2* zhy = nullptr;
+    float* zkf = nullptr;
+    void* zhost = nullptr; size_t zhost_bytes = 0;   // pinned staging
+    cudaEvent_t zev = nullptr; bool zev_pending = false;
+    // scratch intermediate [cap][ny][px]
+    float2* scratch = nullptr;
+    int scap = 0;
+    // optional per-pass timing events (caller-owned)
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+void free_plan(cwo_plan* p) {
+    if (!p) return;
+    cudaFree(p->tw_x);
+    if (p->tw_y != p->tw_x) cudaFree(p->tw_y);
+    cudaFree(p->kb_x); cudaFree(p->kb_y);
+    cudaFree(p->ax); cudaFree(p->ay); cudaFree(p->hx); cudaFree(p->hy); cudaFree(p->kf);
+    cudaFree(p->zax); cudaFree(p->zay); cudaFree(p->zhx); cudaFree(p->zhy); cudaFree(p->zkf);
+    if (p->zhost) cudaFreeHost(p->zhost);
+    if (p->zev) cudaEventDestroy(p->zev);
+    cudaFree(p->scratch);
+    delete p;
+}
+
+cwo_status check_params(int nx, int ny, double dx, double dy, double lambda, double z, int type, unsigned flags) {
+    if (!pow2_side(nx) || !pow2_side(ny))
+        return fail(CWO_ERR_INVALID_ARG, "Nx=%d, Ny=%d: each side must be a power of two in [%d, %d]", nx, ny, CWO_MIN_SIDE, CWO_MAX_SIDE);
+    if (!(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy))
+        return fail(CWO_ERR_INVALID_ARG, "pitches must be finite and > 0 (dx=%g, dy=%g)", dx, dy);
+    if (!(lambda > 0) || !std::isfinite(lambda)) return fail(CWO_ERR_INVALID_ARG, "wavelength must be finite and > 0 (%g)", lambda);
+    if (!std::isfinite(z)) return fail(CWO_ERR_INVALID_ARG, "distance must be finite (%g)", z);
+    if (type == CWO_FRESNEL_FOURIER || type == CWO_SHIFTED_FRESNEL || type == CWO_SHIFTED_ANGULAR)
+        return fail(CWO_ERR_UNSUPPORTED, "diffraction type %d is not provided (only CWO_ANGULAR and CWO_FRESNEL_CONV)", type);
+    if (type != CWO_ANGULAR && type != CWO_FRESNEL_CONV) return fail(CWO_ERR_INVALID_ARG, "unknown diffraction type %d", type);
+    if (type == CWO_FRESNEL_CONV && z == 0.0) return fail(CWO_ERR_INVALID_ARG, "Fresnel diffraction needs z != 0");
+    const unsigned known = CWO_FLAG_PHASE_FP32 | CWO_FLAG_PHASE_FP64 | CWO_FLAG_LITERAL_SCALE;
+    if (flags & ~known) return fail(CWO_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
+    if ((flags & CWO_FLAG_PHASE_FP32) && (flags & CWO_FLAG_PHASE_FP64))
+        return fail(CWO_ERR_INVALID_ARG, "CWO_FLAG_PHASE_FP32 and CWO_FLAG_PHASE_FP64 are exclusive");
+    if ((flags & (CWO_FLAG_PHASE_FP32 | CWO_FLAG_PHASE_FP64)) && type != CWO_ANGULAR)
+        return fail(CWO_ERR_INVALID_ARG, "phase-precision flags apply to CWO_ANGULAR only");
+    if ((flags & CWO_FLAG_LITERAL_SCALE) && type != CWO_FRESNEL_CONV)
+        return fail(CWO_ERR_INVALID_ARG, "CWO_FLAG_LITERAL_SCALE applies to CWO_FRESNEL_CONV only");
+    return CWO_OK;
+}
+
+// host tables of one parameter set
+void host_h_tables(const cwo_plan* p, double z, float4* ax, float4* ay, float2* hx, float2* hy, float* kf) {
+    make_h_tables(p->px, p->py, p->dx, p->dy, p->lambda, z, p->type == CWO_FRESNEL_CONV,
+                  (p->flags & CWO_FLAG_LITERAL_SCALE) != 0, ax, ay, hx, hy, kf);
+}
+
+cwo_status ensure_scratch(cwo_plan* p, int items) {
+    if (items <= p->scap) return CWO_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize before growing scratch");
+    cudaFree(p->scratch);
+    p->scratch = nullptr;
+    p->scap = 0;
+    cwo_status st = dev_alloc(&p->scratch, (size_t)items * p->ny * p->px, "scratch");
+    if (st != CWO_OK) return st;
+    p->scap = items;
+    return CWO_OK;
+}
+
+cwo_status ensure_ztables(cwo_plan* p, int items) {
+    if (items <= p->zcap) return CWO_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize before growing tables");
+    cudaFree(p->zax); cudaFree(p->zay); cudaFree(p->zhx); cudaFree(p->zhy); cudaFree(p->zkf);
+    p->zax = p->zay = nullptr; p->zhx = p->zhy = nullptr; p->zkf = nullptr;
+    if (p->zhost) { cudaFreeHost(p->zhost); p->zhost = nullptr; }
+    p->zcap = 0;
+    cwo_status st;
+    const size_t nx4 = (size_t)items * p->px, ny4 = (size_t)items * p->py;
+    if (p->type == CWO_ANGULAR) {
+        if ((st = dev_alloc(&p->zax, nx4, "per-item x tables")) || (st = dev_alloc(&p->zay, ny4, "per-item y tables")) ||
+            (st = dev_alloc(&p->zkf, (size_t)items, "per-item K")))
+            return st;
+        p->zhost_bytes = (nx4 + ny4) * sizeof(float4) + items * sizeof(float);
+    } else {
+        if ((st = dev_alloc(&p->zhx, nx4, "per-item x tables")) || (st = dev_alloc(&p->zhy, ny4, "per-item y tables")))
+            return st;
+        p->zhost_bytes = (nx4 + ny4) * sizeof(float2);
+    }
+    e = cudaMallocHost(&p->zhost, p->zhost_bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); p->zhost = nullptr; return fail(CWO_ERR_OOM, "pinned staging of %zu bytes failed", p->zhost_bytes); }
+    if (!p->zev) {
+        e = cudaEventCreateWithFlags(&p->zev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
+    p->zcap = items;
+    return CWO_OK;
+}
+
+cwo_status check_plan_device(const cwo_plan* p) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device) return fail(CWO_ERR_INVALID_ARG, "current device %d differs from the plan's device %d", dev, p->device);
+    return CWO_OK;
+}
+
+cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int batch,
+               const double* zs, void* stream, bool adjoint) {
+    if (!p) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
+    if (batch < 1 || batch > 65535) return fail(CWO_ERR_INVALID_ARG, "batch must be in [1, 65535] (got %d)", batch);
+    const long long field = (long long)p->nx * p->ny;
+    if (in_stride < 0) return fail(CWO_ERR_INVALID_ARG, "negative input batch stride");
+    if (in_stride != 0 && in_stride < field) return fail(CWO_ERR_INVALID_ARG, "input batch stride %lld smaller than one field (%lld)", in_stride, field);
+    if (adjoint && in_stride == 0 && batch > 1) return fail(CWO_ERR_INVALID_ARG, "the adjoint takes one input per item (stride > 0)");
+    const bool stack = in_stride == 0 && batch > 1;
+    if (zs) {
+        if (p->flags & (CWO_FLAG_PHASE_FP32 | CWO_FLAG_PHASE_FP64))
+            return fail(CWO_ERR_UNSUPPORTED, "per-item distances are not provided with the phase-precision study flags");
+        for (int i = 0; i < batch; ++i) {
+            if (!std::isfinite(zs[i])) return fail(CWO_ERR_INVALID_ARG, "z[%d] is not finite", i);
+            if (p->type == CWO_FRESNEL_CONV && zs[i] == 0.0) return fail(CWO_ERR_INVALID_ARG, "z[%d] = 0 with Fresnel", i);
+        }
+    }
+    cwo_status st = check_plan_device(p);
+    if (st) return st;
+    const size_t fb = (size_t)field * sizeof(float2);
+    const size_t in_bytes = stack ? fb : (size_t)((batch - 1) * (in_stride ? in_stride : field)) * sizeof(float2) + fb;
+    if ((st = check_device_range(in, in_bytes, p->device, "input"))) return st;
+    if ((st = check_device_range(out, (size_t)batch * fb, p->device, "output"))) return st;
+    const int need = stack ? batch + 1 : batch;
+    if ((st = ensure_scratch(p, need))) return st;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    cwo::HParams hp{};
+    hp.conj = adjoint ? 1 : 0;
+    hp.kbx = p->kb_x;
+    hp.kby = p->kb_y;
+    const double K = p->z / p->lambda;
+    hp.K = K;
+    hp.sx = p->lambda * p->lambda / ((double)p->px * p->dx * (double)p->px * p->dx);
+    hp.sy = p->lambda * p->lambda / ((double)p->py * p->dy * (double)p->py * p->dy);
+    hp.z = p->z;
+    hp.k = 2.0 * kPi / p->lambda;
+    hp.dfx = 1.0 / ((double)p->px * p->dx);
+    hp.dfy = 1.0 / ((double)p->py * p->dy);
+    if (p->type == CWO_FRESNEL_CONV) hp.mode = cwo::HMODE_FRESNEL;
+    else if (p->flags & CWO_FLAG_PHASE_FP32) hp.mode = cwo::HMODE_ASM_FP32;
+    else if (p->flags & CWO_FLAG_PHASE_FP64) hp.mode = cwo::HMODE_ASM_FP64;
+    else hp.mode = cwo::HMODE_ASM_REDUCED;
+
+    if (zs) {
+        if ((st = ensure_ztables(p, batch))) return st;
+        if (p->zev_pending) {   // the staging buffer may still feed the previous upload
+            cudaError_t e = cudaEventSynchronize(p->zev);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+            p->zev_pending = false;
+        }
+        char* hb = (char*)p->zhost;
+        if (p->type == CWO_ANGULAR) {
+            float4* hax = (float4*)hb;
+            float4* hay = hax + (size_t)batch * p->px;
+            float* hkf = (float*)(hay + (size_t)batch * p->py);
+            for (int i = 0; i < batch; ++i)
+                host_h_tables(p, zs[i], hax + (size_t)i * p->px, hay + (size_t)i * p->py, nullptr, nullptr, hkf + i);
+            cudaError_t e;
+            if ((e = cudaMemcpyAsync(p->zax, hax, (size_t)batch * p->px * sizeof(float4), cudaMemcpyHostToDevice, s)) ||
+                (e = cudaMemcpyAsync(p->zay, hay, (size_t)batch * p->py * sizeof(float4), cudaMemcpyHostToDevice, s)) ||
+                (e = cudaMemcpyAsync(p->zkf, hkf, (size_t)batch * sizeof(float), cudaMemcpyHostToDevice, s)))
+                return cuda_fail(e, "table upload");
+            hp.ax = p->zax; hp.ay = p->zay; hp.kf = p->zkf;
+            hp.x_item_stride = p->px; hp.y_item_stride = p->py; hp.kf_item_stride = 1;
+        } else {
+            float2* hhx = (float2*)hb;
+            float2* hhy = hhx + (size_t)batch * p->px;
+            for (int i = 0; i < batch; ++i)
+                host_h_tables(p, zs[i], nullptr, nullptr, hhx + (size_t)i * p->px, hhy + (size_t)i * p->py, nullptr);
+            cudaError_t e;
+            if ((e = cudaMemcpyAsync(p->zhx, hhx, (size_t)batch * p->px * sizeof(float2), cudaMemcpyHostToDevice, s)) ||
+                (e = cudaMemcpyAsync(p->zhy, hhy, (size_t)batch * p->py * sizeof(float2), cudaMemcpyHostToDevice, s)))
+                return cuda_fail(e, "table upload");
+            hp.hx = p->zhx; hp.hy = p->zhy;
+            hp.x_item_stride = p->px; hp.y_item_stride = p->py;
+        }
+        cudaError_t e = cudaEventRecord(p->zev, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        p->zev_pending = true;
+    } else {
+        hp.ax = p->ax; hp.ay = p->ay; hp.kf = p->kf; hp.hx = p->hx; hp.hy = p->hy;
+        hp.x_item_stride = 0; hp.y_item_stride = 0; hp.kf_item_stride = 0;
+    }
+
+    const long long wstride = (long long)p->ny * p->px;
+    const bool timing = p->tev[0] != nullptr;
+    auto mark = [&](int i) { return timing ? cudaEventRecord(p->tev[i], s) : cudaSuccess; };
+    const float2* fin = (const float2*)in;
+    float2* fout = (float2*)out;
+    cudaError_t e;
+    const float scale = (float)(1.0 / ((double)p->px * (double)p->py));
+    if (stack) {
+        // the shared source: row pass once, then per-plane column and inverse row passes
+        float2* w0 = p->scratch;
+        float2* wz = p->scratch + wstride;
+        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, 0, w0, 0, p->ny, 1, p->tw_x, s)) || (e = mark(1)))
+            return cuda_fail(e, "row forward launch");
+        if ((e = cwo::launch_col(p->py, w0, 0, wz, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2)))
+            return cuda_fail(e, "column launch");
+        if ((e = cwo::launch_row_inv(p->px, wz, wstride, fout, field, p->ny, batch, scale, p->tw_x, s)) || (e = mark(3)))
+            return cuda_fail(e, "row inverse launch");
+    } else {
+        const long long istr = in_stride ? in_stride : field;
+        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, istr, p->scratch, wstride, p->ny, batch, p->tw_x, s)) || (e = mark(1)))
+            return cuda_fail(e, "row forward launch");
+        if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2)))
+            return cuda_fail(e, "column launch");
+        if ((e = cwo::launch_row_inv(p->px, p->scratch, wstride, fout, field, p->ny, batch, scale, p->tw_x, s)) || (e = mark(3)))
+            return cuda_fail(e, "row inverse launch");
+    }
+    return CWO_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+const char* cwo_last_error(void) { return g_err.c_str(); }
+
+int cwo_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+cwo_status cwo_plan_device_bytes(int nx, int ny, int batch, size_t* bytes) {
+    if (!bytes) return fail(CWO_ERR_INVALID_ARG, "bytes is NULL");
+    if (!pow2_side(nx) || !pow2_side(ny)) return fail(CWO_ERR_INVALID_ARG, "Nx=%d, Ny=%d out of range", nx, ny);
+    if (batch < 1) return fail(CWO_ERR_INVALID_ARG, "batch must be >= 1");
+    *bytes = tables_bytes(nx, ny) + (size_t)batch * ny * (2 * (size_t)nx) * sizeof(float2);
+    return CWO_OK;
+}
+
+cwo_status cwo_plan_create(int nx, int ny, double dx, double dy, double lambda, double z,
+                           cwo_type type, unsigned flags, cwo_plan** out) {
+    if (!out) return fail(CWO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    cwo_status st = check_params(nx, ny, dx, dy, lambda, z, (int)type, flags);
+    if (st) return st;
+    cwo_plan* p = new (std::nothrow) cwo_plan();
+    if (!p) return fail(CWO_ERR_OOM, "host allocation failed");
+    p->nx = nx; p->ny = ny; p->px = 2 * nx; p->py = 2 * ny;
+    p->dx = dx; p->dy = dy; p->lambda = lambda; p->z = z; p->type = type; p->flags = flags;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaGetDevice"); }
+
+    const AxisGeo gx(p->px), gy(p->py);
+    const std::vector<float2> twx = twiddle_table(gx);
+    const std::vector<int> kbx = bin_table(gx), kby = bin_table(gy);
+    if ((st = dev_alloc(&p->tw_x, twx.size(), "x twiddles")) || (st = upload(p->tw_x, twx, "x twiddle upload"))) { free_plan(p); return st; }
+    if (p->py == p->px) {
+        p->tw_y = p->tw_x;
+    } else {
+        const std::vector<float2> twy = twiddle_table(gy);
+        if ((st = dev_alloc(&p->tw_y, twy.size(), "y twiddles")) || (st = upload(p->tw_y, twy, "y twiddle upload"))) { free_plan(p); return st; }
+    }
+    if ((st = dev_alloc(&p->kb_x, kbx.size(), "x bins")) || (st = upload(p->kb_x, kbx, "x bin upload")) ||
+        (st = dev_alloc(&p->kb_y, kby.size(), "y bins")) || (st = upload(p->kb_y, kby, "y bin upload"))) { free_plan(p); return st; }
+    if (type == CWO_ANGULAR) {
+        std::vector<float4> ax(p->px), ay(p->py);
+        std::vector<float> kf(1);
+        host_h_tables(p, z, ax.data(), ay.data(), nullptr, nullptr, kf.data());
+        if ((st = dev_alloc(&p->ax, ax.size(), "x table")) || (st = upload(p->ax, ax, "x table upload")) ||
+            (st = dev_alloc(&p->ay, ay.size(), "y table")) || (st = upload(p->ay, ay, "y table upload")) ||
+            (st = dev_alloc(&p->kf, kf.size(), "K")) || (st = upload(p->kf, kf, "K upload"))) { free_plan(p); return st; }
+    } else {
+        std::vector<float2> hx(p->px), hy(p->py);
+        host_h_tables(p, z, nullptr, nullptr, hx.data(), hy.data(), nullptr);
+        if ((st = dev_alloc(&p->hx, hx.size(), "x table")) || (st = upload(p->hx, hx, "x table upload")) ||
+            (st = dev_alloc(&p->hy, hy.size(), "y table")) || (st = upload(p->hy, hy, "y table upload"))) { free_plan(p); return st; }
+    }
+    if ((st = ensure_scratch(p, 1))) { free_plan(p); return st; }
+    *out = p;
+    return CWO_OK;
+}
+
+cwo_status cwo_plan_destroy(cwo_plan* plan) {
+    free_plan(plan);
+    return CWO_OK;
+}
+
+cwo_status cwo_plan_reserve(cwo_plan* plan, int batch) {
+    if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
+    if (batch < 1 || batch > 65535) return fail(CWO_ERR_INVALID_ARG, "batch must be in [1, 65535]");
+    cwo_status st = check_plan_device(plan);
+    if (st) return st;
+    return ensure_scratch(plan, batch + 1);
+}
+
+cwo_status cwo_propagate(cwo_plan* plan, const void* in_c64, void* out_c64, void* cuda_stream) {
+    if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
+    return run(plan, in_c64, (long long)plan->nx * plan->ny, out_c64, 1, nullptr, cuda_stream, false);
+}
+
+cwo_status cwo_propagate_batch(cwo_plan* plan, const void* in, long long in_batch_stride, void* out,
+                               int batch, const double* z_or_null, void* cuda_stream) {
+    return run(plan, in, in_batch_stride, out, batch, z_or_null, cuda_stream, false);
+}
+
+cwo_status cwo_propagate_adjoint(cwo_plan* plan, const void* in_c64, void* out_c64, void* cuda_stream) {
+    if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
+    return run(plan, in_c64, (long long)plan->nx * plan->ny, out_c64, 1, nullptr, cuda_stream, true);
+}
+
+cwo_status cwo_propagate_adjoint_batch(cwo_plan* plan, const void* in, long long in_batch_stride,
+                                       void* out, int batch, const double* z_or_null, void* cuda_stream) {
+    if (in_batch_stride == 0) return fail(CWO_ERR_INVALID_ARG, "the adjoint takes one input per item (stride > 0)");
+    return run(plan, in, in_batch_stride, out, batch, z_or_null, cuda_stream, true);
+}
+
+int cwo_launches_per_call(const cwo_plan* plan) { return plan ? 3 : 0; }
+
+cwo_status cwo_plan_set_timing_events(cwo_plan* plan, void* const* events) {
+    if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
+    for (int i = 0; i < 4; ++i) plan->tev[i] = events ? (cudaEvent_t)events[i] : nullptr;
+    if (events)
+        for (int i = 0; i < 4; ++i)
+            if (!plan->tev[i]) { for (auto& ev : plan->tev) ev = nullptr; return fail(CWO_ERR_INVALID_ARG, "events[%d] is NULL", i); }
+    return CWO_OK;
+}
+
+// ---------------------------------------------------------------- host-only diagnostics
+cwo_status cwo_debug_axis_bins(int p, int* bins) {
+    if (!bins || p < 32 || p > 8192 || (p & (p - 1))) return fail(CWO_ERR_INVALID_ARG, "bad axis length");
+    const AxisGeo g(p);
+    for (int i = 0; i < p; ++i) bins[i] = g.freq_of_idx(i);
+    return CWO_OK;
+}
+
+cwo_status cwo_debug_fresnel_axis(int p, double pitch, double lambda, double z, double* out_ri) {
+    if (!out_ri || p < 2 || (p & (p - 1)) || !(pitch > 0) || !(lambda > 0) || z == 0.0)
+        return fail(CWO_ERR_INVALID_ARG, "bad arguments");
+    const std::vector<cd> h = fresnel_axis_dft(p, pitch, lambda, z);
+    for (int i = 0; i < p; ++i) { out_ri[2 * i] = h[i].real(); out_ri[2 * i + 1] = h[i].imag(); }
+    return CWO_OK;
+}
+
+cwo_status cwo_debug_twiddles(int p, float* out_ri) {
+    if (!out_ri || p < 32 || p > 8192 || (p & (p - 1))) return fail(CWO_ERR_INVALID_ARG, "bad axis length");
+    const AxisGeo g(p);
+    const std::vector<float2> tw = twiddle_table(g);
+    for (size_t i = 0; i < tw.size(); ++i) { out_ri[2 * i] = tw[i].x; out_ri[2 * i + 1] = tw[i].y; }
+    return CWO_OK;
+}
+
+cwo_status cwo_debug_asm_axis(int p, double pitch, double lambda, double z, int is_x, float* out4) {
+    if (!out4 || p < 32 || p > 8192 || (p & (p - 1)) || !(pitch > 0) || !(lambda > 0))
+        return fail(CWO_ERR_INVALID_ARG, "bad arguments");
+    const AxisGeo g(p);
+    asm_axis_table(g, pitch, lambda, z, is_x != 0, (float4*)out4);
+    return CWO_OK;
+}
+
+}  // extern "C"

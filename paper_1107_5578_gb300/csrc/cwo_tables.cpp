@@ -1,0 +1,146 @@
+// cwo_tables.cpp -- FP64 host computation of the per-plan tables.
+//
+//  * axis permutation: the forward FFT leaves frequency k at its DIF (digit-reversed) position;
+//    the passes store and index it by axis index idx = e*T + t (register e of thread t).
+//  * twiddles W_{L_s}^{(t mod S_s) k} of every radix-16 stage, correctly rounded from FP64.
+//  * Fresnel (Eq. fre_conv_fft): the separable factors of FFT[h_F] -- 1-D DFTs of
+//    h(d) = exp(i pi (d pitch)^2 / (lambda z)) over the padded axis -- and C, with every phase
+//    reduced modulo one cycle in FP64.
+//  * angular spectrum (Eq. ang2): per-axis parts of the phase K sqrt(1 - s), K = z / lambda,
+//    reduced modulo one cycle in FP64 (see cwo_h.cuh for the split).
+#include "cwo_tables.h"
+
+#include <cmath>
+
+#include "../../include/cwo.h"
+
+namespace cwo {
+namespace host {
+
+namespace {
+constexpr double kPi = 3.14159265358979323846264338327950288;
+int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+}  // namespace
+
+double frac01(double x) { return x - std::floor(x); }
+
+AxisGeo::AxisGeo(int p) : P(p), T(p / 16) {
+    const int lg = ilog2i(p);
+    NST = (lg + 3) / 4;
+    RLAST = 1 << (lg - 4 * (NST - 1));
+}
+
+// pos = sum_s k_s P / (r_0..r_s)  and  k = sum_s k_s (r_0..r_{s-1})
+int AxisGeo::freq_of_pos(int pos) const {
+    int k = 0, below = 1, above = P;
+    for (int s = 0; s < NST; ++s) {
+        const int r = radix(s);
+        above /= r;
+        const int ks = (pos / above) % r;
+        k += ks * below;
+        below *= r;
+    }
+    return k;
+}
+
+std::vector<float2> twiddle_table(const AxisGeo& g) {
+    std::vector<float2> tw((size_t)(g.NST > 1 ? g.NST - 1 : 0) * g.P);
+    for (int s = 0; s + 1 < g.NST; ++s) {
+        const int L = g.len(s), S = g.stride(s);
+        for (int k = 0; k < 16; ++k)
+            for (int t = 0; t < g.T; ++t) {
+                const long long jk = (long long)(t % S) * k % L;
+                const double ang = -2.0 * kPi * (double)jk / (double)L;
+                tw[(size_t)s * g.P + (size_t)k * g.T + t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            }
+    }
+    return tw;
+}
+
+std::vector<int> bin_table(const AxisGeo& g) {
+    std::vector<int> b(g.P);
+    for (int i = 0; i < g.P; ++i) b[i] = g.signed_bin(g.freq_of_idx(i));
+    return b;
+}
+
+// FP64 Stockham radix-2 FFT, forward sign, out-of-place ping-pong
+void fft64(std::vector<cd>& x) {
+    const int n = (int)x.size();
+    std::vector<cd> y(n);
+    for (int l = n / 2, m = 1; l >= 1; l /= 2, m *= 2) {
+        for (int j = 0; j < l; ++j) {
+            const double ang = -kPi * (double)j / (double)l;
+            const cd w(std::cos(ang), std::sin(ang));
+            for (int k = 0; k < m; ++k) {
+                const cd c0 = x[k + j * m], c1 = x[k + j * m + l * m];
+                y[k + 2 * j * m] = c0 + c1;
+                y[k + 2 * j * m + m] = (c0 - c1) * w;
+            }
+        }
+        x.swap(y);
+    }
+}
+
+std::vector<cd> fresnel_axis_dft(int P, double pitch, double lambda, double z) {
+    std::vector<cd> h(P);
+    const double c = pitch * pitch / (2.0 * lambda * z);   // cycles per d^2
+    for (int i = 0; i < P; ++i) {
+        const double d = (double)(i < P / 2 ? i : i - P);
+        const double ph = frac01(c * d * d);
+        h[i] = cd(std::cos(2.0 * kPi * ph), std::sin(2.0 * kPi * ph));
+    }
+    fft64(h);
+    return h;
+}
+
+cd fresnel_coeff(double dx, double dy, double lambda, double z, bool literal_scale) {
+    const double ph = frac01(z / lambda);
+    cd c = cd(std::cos(2.0 * kPi * ph), std::sin(2.0 * kPi * ph)) / cd(0.0, lambda * z);
+    if (!literal_scale) c *= dx * dy;
+    return c;
+}
+
+void asm_axis_table(const AxisGeo& g, double pitch, double lambda, double z, bool is_x, float4* out) {
+    const double K = z / lambda;
+    const double c0 = is_x ? frac01(K) : 0.0;
+    const double sgn = (is_x && K < 0) ? -1.0 : 1.0;
+    const double rt = std::sqrt(std::fabs(K)) * 0.5;
+    const double Pd = (double)g.P * pitch;
+    const double c1 = z * lambda / (2.0 * Pd * Pd);                              // K a / 2   per kt^2
+    const double c2 = z * lambda * lambda * lambda / (8.0 * Pd * Pd * Pd * Pd);  // K a^2 / 8 per kt^4
+    for (int i = 0; i < g.P; ++i) {
+        const double kt = (double)g.signed_bin(g.freq_of_idx(i));
+        const double k2 = kt * kt;
+        const double a = lambda * lambda * k2 / (Pd * Pd);
+        const double W = frac01(frac01(c1 * k2) + frac01(c2 * k2 * k2)) - c0;
+        const double u = sgn * rt * a;
+        const float uh = (float)u;
+        const float ul = (float)(u - (double)uh);
+        out[i] = make_float4((float)a, (float)W, uh, ul);
+    }
+}
+
+void make_h_tables(int px, int py, double dx, double dy, double lambda, double z, bool fresnel,
+                   bool literal_scale, float4* ax, float4* ay, float2* hx, float2* hy, float* kf) {
+    const AxisGeo gx(px), gy(py);
+    if (!fresnel) {
+        asm_axis_table(gx, dx, lambda, z, true, ax);
+        asm_axis_table(gy, dy, lambda, z, false, ay);
+        *kf = (float)(z / lambda);
+    } else {
+        const std::vector<cd> Hx = fresnel_axis_dft(px, dx, lambda, z);
+        const std::vector<cd> Hy = fresnel_axis_dft(py, dy, lambda, z);
+        const cd C = fresnel_coeff(dx, dy, lambda, z, literal_scale);
+        for (int i = 0; i < px; ++i) {
+            const cd v = C * Hx[gx.freq_of_idx(i)];
+            hx[i] = make_float2((float)v.real(), (float)v.imag());
+        }
+        for (int i = 0; i < py; ++i) {
+            const cd v = Hy[gy.freq_of_idx(i)];
+            hy[i] = make_float2((float)v.real(), (float)v.imag());
+        }
+    }
+}
+
+}  // namespace host
+}  // namespace cwo

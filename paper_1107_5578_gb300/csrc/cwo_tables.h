@@ -1,0 +1,44 @@
+// cwo_tables.h -- FP64 host computation of the per-plan tables (twiddles, axis permutation,
+// transfer-function factors).  Shared by the plan code and the host emulator.
+#pragma once
+#include <cuda_runtime.h>
+#include <complex>
+#include <vector>
+
+namespace cwo {
+namespace host {
+
+using cd = std::complex<double>;
+
+// Axis geometry, mirrored from the device FFT (cwo_fft.cuh): T = P/16 threads, stages of radix
+// 16 followed by one stage of radix RLAST.  Axis index idx = e*T + t <-> DIF position 16 t + e.
+struct AxisGeo {
+    int P, T, NST, RLAST;
+    explicit AxisGeo(int p);
+    int radix(int s) const { return s == NST - 1 ? RLAST : 16; }
+    int len(int s) const { return P >> (4 * s); }
+    int stride(int s) const { return len(s) / radix(s); }
+    int freq_of_pos(int pos) const;   // bin whose forward DIF output lands at position pos
+    int freq_of_idx(int idx) const { return freq_of_pos(16 * (idx % T) + idx / T); }
+    int signed_bin(int k) const { return k < P / 2 ? k : k - P; }
+};
+
+double frac01(double x);
+std::vector<float2> twiddle_table(const AxisGeo& g);
+std::vector<int> bin_table(const AxisGeo& g);
+void fft64(std::vector<cd>& x);
+std::vector<cd> fresnel_axis_dft(int P, double pitch, double lambda, double z);
+cd fresnel_coeff(double dx, double dy, double lambda, double z, bool literal_scale);
+void asm_axis_table(const AxisGeo& g, double pitch, double lambda, double z, bool is_x, float4* out);
+
+// transfer-function tables of one parameter set, in axis-index order
+struct HTables {
+    std::vector<float4> ax, ay;   // angular spectrum
+    std::vector<float2> hx, hy;   // Fresnel (hx includes C)
+    float K = 0.f;                // z / lambda (angular spectrum tail term)
+};
+void make_h_tables(int px, int py, double dx, double dy, double lambda, double z, bool fresnel,
+                   bool literal_scale, float4* ax, float4* ay, float2* hx, float2* hy, float* kf);
+
+}  // namespace host
+}  // namespace cwo

@@ -1,0 +1,272 @@
+"""Thin Python binding of libcwo_gb300.so (the C ABI of include/cwo.h).
+
+Argument marshalling only: every step of a propagation runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.  If the shared library has not been built the
+import of this module's functions fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcwo_gb300.so")
+
+# cwo_type
+ANGULAR = 0
+FRESNEL_CONV = 1
+FRESNEL_FOURIER = 2
+SHIFTED_FRESNEL = 3
+SHIFTED_ANGULAR = 4
+# flags
+FLAG_PHASE_FP32 = 0x1
+FLAG_PHASE_FP64 = 0x2
+FLAG_LITERAL_SCALE = 0x4
+# status
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = range(6)
+STATUS_NAMES = {0: "CWO_OK", 1: "CWO_ERR_INVALID_ARG", 2: "CWO_ERR_UNSUPPORTED", 3: "CWO_ERR_OOM",
+                4: "CWO_ERR_CUDA", 5: "CWO_ERR_TIMEOUT"}
+DEFAULT_WAVELENGTH = 633e-9
+DEFAULT_PITCH = 10e-6
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CwoError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+def lib() -> ctypes.CDLL:
+    """Load the shared library (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it first "
+                                  "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i, u, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double, ctypes.c_longlong
+            pp = ctypes.POINTER(ctypes.c_void_p)
+            sz = ctypes.POINTER(ctypes.c_size_t)
+            dpp = ctypes.POINTER(ctypes.c_double)
+            sig = {
+                "cwo_plan_create": ([i, i, d, d, d, d, i, u, pp], i),
+                "cwo_plan_destroy": ([vp], i),
+                "cwo_plan_device_bytes": ([i, i, i, sz], i),
+                "cwo_plan_reserve": ([vp, i], i),
+                "cwo_propagate": ([vp, vp, vp, vp], i),
+                "cwo_propagate_batch": ([vp, vp, ll, vp, i, dpp, vp], i),
+                "cwo_propagate_adjoint": ([vp, vp, vp, vp], i),
+                "cwo_propagate_adjoint_batch": ([vp, vp, ll, vp, i, dpp, vp], i),
+                "cwo_launches_per_call": ([vp], i),
+                "cwo_plan_set_timing_events": ([vp, ctypes.POINTER(ctypes.c_void_p)], i),
+                "cwo_last_error": ([], ctypes.c_char_p),
+                "cwo_version": ([], i),
+                "cwo_debug_axis_bins": ([i, vp], i),
+                "cwo_debug_fresnel_axis": ([i, d, d, d, vp], i),
+                "cwo_debug_twiddles": ([i, vp], i),
+                "cwo_debug_asm_axis": ([i, d, d, d, i, vp], i),
+                "cwo_debug_emulate": ([i, i, d, d, d, d, i, u, i, vp, vp], i),
+                "cwo_debug_line_fft": ([i, i, vp, vp], i),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().cwo_last_error().decode("utf-8", "replace")
+
+
+def check(status: int, where: str) -> None:
+    if status != OK:
+        raise CwoError(status, where, last_error())
+
+
+def device_bytes(nx: int, ny: int, batch: int = 1) -> int:
+    out = ctypes.c_size_t(0)
+    check(lib().cwo_plan_device_bytes(nx, ny, batch, ctypes.byref(out)), "cwo_plan_device_bytes")
+    return int(out.value)
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(int(s.cuda_stream))
+
+
+def _check_field(t, nx: int, ny: int, name: str, batch: int | None = None):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.complex64:
+        raise TypeError(f"{name} must be complex64 (got {t.dtype})")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape[-2:]) != (ny, nx):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected [..., {ny}, {nx}]")
+    if batch is not None and t.numel() != batch * nx * ny:
+        raise ValueError(f"{name} holds {t.numel() // (nx * ny)} fields, expected {batch}")
+
+
+class Plan:
+    """A propagation plan (tables resident on the device, scratch owned by the plan)."""
+
+    def __init__(self, nx: int, ny: int | None = None, dx: float = DEFAULT_PITCH,
+                 dy: float | None = None, wavelength: float = DEFAULT_WAVELENGTH, z: float = 0.1,
+                 kind: int = ANGULAR, flags: int = 0):
+        self.nx, self.ny = int(nx), int(nx if ny is None else ny)
+        self.dx, self.dy = float(dx), float(dx if dy is None else dy)
+        self.wavelength, self.z, self.kind, self.flags = float(wavelength), float(z), int(kind), int(flags)
+        h = ctypes.c_void_p(0)
+        check(lib().cwo_plan_create(self.nx, self.ny, self.dx, self.dy, self.wavelength, self.z,
+                                    self.kind, self.flags, ctypes.byref(h)), "cwo_plan_create")
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None or not self._h.value:
+            raise RuntimeError("plan has been destroyed")
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().cwo_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, batch: int) -> None:
+        check(lib().cwo_plan_reserve(self.handle, int(batch)), "cwo_plan_reserve")
+
+    def set_timing_events(self, events) -> None:
+        """Record 4 torch.cuda.Event (enable_timing=True) around the passes of every later call
+        (None switches it off): events[0] before the row forward pass, [1] after it, [2] after
+        the column pass, [3] after the row inverse pass."""
+        if events is None:
+            check(lib().cwo_plan_set_timing_events(self.handle, None), "cwo_plan_set_timing_events")
+            self._events = None
+            return
+        if len(events) != 4:
+            raise ValueError("need 4 events")
+        import torch
+        for ev in events:
+            if not ev.cuda_event:   # torch creates the cudaEvent_t on first record
+                ev.record(torch.cuda.current_stream())
+        arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(ev.cuda_event) for ev in events])
+        check(lib().cwo_plan_set_timing_events(self.handle, arr), "cwo_plan_set_timing_events")
+        self._events = list(events)
+
+    @property
+    def launches_per_call(self) -> int:
+        return int(lib().cwo_launches_per_call(self.handle))
+
+    def _out(self, x, batch_shape):
+        import torch
+        return torch.empty((*batch_shape, self.ny, self.nx), dtype=torch.complex64, device=x.device)
+
+    def propagate(self, x, out=None, stream=None):
+        """One field [Ny][Nx] (complex64, CUDA) -> propagated field."""
+        _check_field(x, self.nx, self.ny, "input", 1)
+        out = self._out(x, x.shape[:-2]) if out is None else out
+        _check_field(out, self.nx, self.ny, "output", 1)
+        check(lib().cwo_propagate(self.handle, ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "cwo_propagate")
+        return out
+
+    def adjoint(self, x, out=None, stream=None):
+        _check_field(x, self.nx, self.ny, "input", 1)
+        out = self._out(x, x.shape[:-2]) if out is None else out
+        _check_field(out, self.nx, self.ny, "output", 1)
+        check(lib().cwo_propagate_adjoint(self.handle, ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+              "cwo_propagate_adjoint")
+        return out
+
+    def propagate_batch(self, x, z=None, out=None, stream=None, adjoint=False):
+        """Batch [B][Ny][Nx] -> [B][Ny][Nx].  ``z``: None (plan z) or B distances (host floats)."""
+        b = x.shape[0] if x.dim() == 3 else 1
+        _check_field(x, self.nx, self.ny, "input", b)
+        return self._batch(x, self.nx * self.ny, b, z, out, stream, adjoint)
+
+    def propagate_stack(self, x, zs, out=None, stream=None):
+        """One source [Ny][Nx] propagated to len(zs) planes in one batched call (shared spectrum)."""
+        _check_field(x, self.nx, self.ny, "input", 1)
+        return self._batch(x, 0, len(zs), zs, out, stream, False)
+
+    def _batch(self, x, stride, b, z, out, stream, adjoint):
+        out = self._out(x, (b,)) if out is None else out
+        _check_field(out, self.nx, self.ny, "output", b)
+        zp = None
+        if z is not None:
+            if len(z) != b:
+                raise ValueError(f"{len(z)} distances for {b} items")
+            zarr = (ctypes.c_double * b)(*[float(v) for v in z])
+            zp = ctypes.cast(zarr, ctypes.POINTER(ctypes.c_double))
+        fn = lib().cwo_propagate_adjoint_batch if adjoint else lib().cwo_propagate_batch
+        check(fn(self.handle, ctypes.c_void_p(x.data_ptr()), int(stride), ctypes.c_void_p(out.data_ptr()),
+                 int(b), zp, _stream_handle(stream)), fn.__name__)
+        return out
+
+
+def emulate(u, dx, dy, wavelength, z, kind=ANGULAR, flags=0, adjoint=False):
+    """Host emulation of the kernels (test support): numpy complex64 [ny][nx] -> same."""
+    import numpy as np
+    a = np.ascontiguousarray(u, dtype=np.complex64)
+    ny, nx = a.shape
+    out = np.empty_like(a)
+    check(lib().cwo_debug_emulate(nx, ny, dx, dy, wavelength, z, kind, flags, int(adjoint),
+                                  a.ctypes.data, out.ctypes.data), "cwo_debug_emulate")
+    return out
+
+
+def line_fft(x, inverse=False):
+    """Host emulation of one padded line transform (test support)."""
+    import numpy as np
+    a = np.ascontiguousarray(x, dtype=np.complex64)
+    p = a.size if inverse else 2 * a.size
+    out = np.empty(p // 2 if inverse else p, dtype=np.complex64)
+    check(lib().cwo_debug_line_fft(p, int(inverse), a.ctypes.data, out.ctypes.data), "cwo_debug_line_fft")
+    return out
+
+
+def axis_bins(p: int):
+    import numpy as np
+    out = np.empty(p, dtype=np.int32)
+    check(lib().cwo_debug_axis_bins(p, out.ctypes.data), "cwo_debug_axis_bins")
+    return out
+
+
+def fresnel_axis(p: int, pitch: float, wavelength: float, z: float):
+    import numpy as np
+    out = np.empty(p, dtype=np.complex128)
+    check(lib().cwo_debug_fresnel_axis(p, pitch, wavelength, z, out.ctypes.data), "cwo_debug_fresnel_axis")
+    return out
+
+
+def twiddles(p: int):
+    import numpy as np
+    nst = (int(p).bit_length() - 1 + 3) // 4
+    out = np.empty(max(nst - 1, 0) * p, dtype=np.complex64)
+    check(lib().cwo_debug_twiddles(p, out.ctypes.data), "cwo_debug_twiddles")
+    return out
+
+
+def asm_axis(p: int, pitch: float, wavelength: float, z: float, is_x: bool):
+    import numpy as np
+    out = np.empty((p, 4), dtype=np.float32)
+    check(lib().cwo_debug_asm_axis(p, pitch, wavelength, z, int(is_x), out.ctypes.data), "cwo_debug_asm_axis")
+    return out

@@ -1,0 +1,196 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Bar: relative L2 error <= 2e-5 (FP32 field/FFT arithmetic against FP64)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_5578_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def cwo(gpu):
+    import paper_1107_5578_gb300.cwo as m
+    m.lib()
+    return m
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def to_dev(u):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(u, dtype=np.complex64)).cuda()
+
+
+def to_host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def gpu_prop(cwo, u, dx, dy, lam, z, kind, flags=0, adjoint=False):
+    ny, nx = u.shape
+    plan = cwo.Plan(nx, ny, dx, dy, lam, z, kind, flags)
+    x = to_dev(u)
+    y = plan.adjoint(x) if adjoint else plan.propagate(x)
+    out = to_host(y)
+    plan.close()
+    return out
+
+
+ORC_KIND = {0: oracle.ANGULAR, 1: oracle.FRESNEL_CONV}
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 256, 512, 1024])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_square_sizes(cwo, n, kind):
+    u = synth.random_field(n, seed=100 + n)
+    z = 0.05 if kind == 0 else 0.08
+    got = gpu_prop(cwo, u, 10e-6, 10e-6, 633e-9, z, kind)
+    want = oracle.propagate(u, 10e-6, 10e-6, 633e-9, z, ORC_KIND[kind])
+    assert rel(got, want) <= TOL
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 16), (16, 128), (256, 32), (32, 512), (2048, 16)])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_rectangular(cwo, nx, ny, kind):
+    u = synth.random_field(nx, seed=7, ny=ny)
+    got = gpu_prop(cwo, u, 8e-6, 6e-6, 532e-9, 0.03, kind)
+    want = oracle.propagate(u, 8e-6, 6e-6, 532e-9, 0.03, ORC_KIND[kind])
+    assert rel(got, want) <= TOL
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("n", [32, 256])
+def test_adjoint(cwo, kind, n):
+    u = synth.random_field(n, seed=5)
+    got = gpu_prop(cwo, u, 10e-6, 10e-6, 633e-9, 0.07, kind, adjoint=True)
+    want = oracle.propagate(u, 10e-6, 10e-6, 633e-9, 0.07, ORC_KIND[kind], oracle.ADJOINT)
+    assert rel(got, want) <= TOL
+
+
+def test_asm_512_config(cwo):
+    # 512 x 512 field, amplitude U[0,1), phase U[0, 2 pi), padded to 1024^2, 633 nm, 10 um, 5 cm
+    u = synth.random_field(512, seed=1)
+    got = gpu_prop(cwo, u, 10e-6, 10e-6, 633e-9, 0.05, 0)
+    want = oracle.propagate(u, 10e-6, 10e-6, 633e-9, 0.05, oracle.ANGULAR)
+    assert rel(got, want) <= TOL
+
+
+def test_asm_zero_distance_identity(cwo):
+    u = synth.random_field(128, seed=3)
+    got = gpu_prop(cwo, u, 10e-6, 10e-6, 633e-9, 0.0, 0)
+    assert rel(got, u) <= 2e-6
+
+
+def test_asm_negative_distance(cwo):
+    u = synth.random_field(128, seed=4)
+    got = gpu_prop(cwo, u, 10e-6, 10e-6, 633e-9, -0.12, 0)
+    want = oracle.propagate(u, 10e-6, 10e-6, 633e-9, -0.12, oracle.ANGULAR)
+    assert rel(got, want) <= TOL
+
+
+def test_asm_evanescent(cwo):
+    # pitch below lambda / sqrt(2): the corners of the band are evanescent and cut
+    u = synth.random_field(64, seed=6)
+    got = gpu_prop(cwo, u, 0.4e-6, 0.4e-6, 633e-9, 20e-6, 0)
+    want = oracle.propagate(u, 0.4e-6, 0.4e-6, 633e-9, 20e-6, oracle.ANGULAR)
+    assert rel(got, want) <= TOL
+
+
+def test_fresnel_literal_scale(cwo):
+    u = synth.random_field(64, seed=8)
+    got = gpu_prop(cwo, u, 10e-6, 10e-6, 633e-9, 0.05, 1, flags=cwo.FLAG_LITERAL_SCALE)
+    want = oracle.propagate(u, 10e-6, 10e-6, 633e-9, 0.05, oracle.FRESNEL_CONV, oracle.LITERAL_SCALE)
+    assert rel(got, want) <= TOL
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_batch_per_item_z(cwo, kind):
+    import torch
+    n, b = 128, 5
+    zs = [0.01, 0.05, 0.1, 0.2, 0.35]
+    us = np.stack([synth.random_field(n, seed=20 + i) for i in range(b)])
+    plan = cwo.Plan(n, None, 8e-6, None, 532e-9, 0.1, kind)
+    y = to_host(plan.propagate_batch(to_dev(us), z=zs))
+    for i in range(b):
+        want = oracle.propagate(us[i], 8e-6, 8e-6, 532e-9, zs[i], ORC_KIND[kind])
+        assert rel(y[i], want) <= TOL
+    # the same batch again with the plan's z equals independent single calls bit for bit
+    yb = plan.propagate_batch(to_dev(us))
+    for i in range(b):
+        single = plan.propagate(to_dev(us[i]))
+        assert torch.equal(yb[i], single)
+    plan.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_stack_shared_source(cwo, kind):
+    n = 128
+    zs = list(np.linspace(0.1, 0.4, 6))
+    u = synth.masked_gaussian(n, seed=2, sigma_px=25.0)
+    plan = cwo.Plan(n, None, 8e-6, None, 532e-9, 0.1, kind)
+    y = to_host(plan.propagate_stack(to_dev(u), zs))
+    for i, z in enumerate(zs):
+        want = oracle.propagate(u, 8e-6, 8e-6, 532e-9, float(z), ORC_KIND[kind])
+        assert rel(y[i], want) <= TOL
+    plan.close()
+
+
+def test_in_place(cwo):
+    u = synth.random_field(64, seed=9)
+    plan = cwo.Plan(64, None, 10e-6, None, 633e-9, 0.05, 0)
+    x = to_dev(u)
+    plan.propagate(x, out=x)
+    want = oracle.propagate(u, 10e-6, 10e-6, 633e-9, 0.05, oracle.ANGULAR)
+    assert rel(to_host(x), want) <= TOL
+    plan.close()
+
+
+def test_rejects_host_and_short_buffers(cwo):
+    import torch
+    plan = cwo.Plan(64, None, 10e-6, None, 633e-9, 0.05, 0)
+    x = torch.zeros(64, 64, dtype=torch.complex64)
+    host = x.numpy()
+    out = torch.zeros(64, 64, dtype=torch.complex64, device="cuda")
+    st = cwo.lib().cwo_propagate(plan.handle, host.ctypes.data, out.data_ptr(), None)
+    assert st == cwo.ERR_INVALID_ARG
+    short = torch.zeros(100, dtype=torch.complex64, device="cuda")
+    # a buffer whose allocation is too small for a field is refused before any launch
+    big = torch.zeros(1 << 20, dtype=torch.complex64, device="cuda")
+    end = big.data_ptr() + big.numel() * 8 - 100 * 8
+    st = cwo.lib().cwo_propagate(plan.handle, end, out.data_ptr(), None)
+    del short
+    if st != cwo.OK:       # the caching allocator may hand out a larger segment
+        assert st == cwo.ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    plan.close()
+
+
+# ---------------------------------------------------------------------- full-size workloads
+
+@pytest.mark.slow
+def test_asm_2048_full(cwo):
+    u = synth.random_field(2048, seed=11)
+    got = gpu_prop(cwo, u, 10e-6, 10e-6, 633e-9, 0.05, 0)
+    want = oracle.propagate(u, 10e-6, 10e-6, 633e-9, 0.05, oracle.ANGULAR)
+    assert rel(got, want) <= TOL
+
+
+@pytest.mark.slow
+def test_fresnel_stack_2048_sampled_planes(cwo):
+    # 2048^2 binary mask (p = 0.5) x Gaussian (sigma 400 px), 532 nm, 8 um, 16 planes z in [0.1, 0.4]
+    n = 2048
+    zs = np.linspace(0.1, 0.4, 16)
+    u = synth.masked_gaussian(n, seed=2)
+    plan = cwo.Plan(n, None, 8e-6, None, 532e-9, 0.1, 1)
+    y = plan.propagate_stack(to_dev(u), list(zs))
+    for j in (0, 7, 15):
+        want = oracle.propagate(u, 8e-6, 8e-6, 532e-9, float(zs[j]), oracle.FRESNEL_CONV)
+        assert rel(to_host(y[j]), want) <= TOL
+    plan.close()

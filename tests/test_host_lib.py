@@ -1,0 +1,161 @@
+"""Host-only checks of libcwo_gb300.so: exports, argument validation, FP64 tables, and the
+host emulation of the kernels against the oracle.  No GPU needed."""
+import ctypes
+import json
+import os
+import re
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_5578_gb300 import cwo, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1107_5578_gb300 import build
+    build.build()
+    return cwo.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(cwo_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_and_default_constants(lib):
+    assert lib.cwo_version() >= 10000
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_defaults.json")))
+    assert cwo.DEFAULT_WAVELENGTH == gold["wavelength_m"]
+    assert cwo.DEFAULT_PITCH == gold["pitch_m"]
+    hdr = open(os.path.join(ROOT, "include", "cwo.h")).read()
+    assert re.search(r"#define CWO_DEFAULT_WAVELENGTH 633e-9", hdr)
+    assert re.search(r"#define CWO_DEFAULT_PITCH 10e-6", hdr)
+
+
+@pytest.mark.parametrize("nx,ny,batch", [(16, 16, 1), (2048, 2048, 16), (4096, 1024, 3)])
+def test_device_bytes_is_host_only(lib, nx, ny, batch):
+    b = cwo.device_bytes(nx, ny, batch)
+    assert b >= batch * ny * 2 * nx * 8            # the 2Nx-wide intermediate per field
+    assert b < batch * ny * 2 * nx * 8 + (1 << 22)
+
+
+@pytest.mark.parametrize("args,status", [
+    ((12, 16, 1e-5, 1e-5, 633e-9, 0.1, 0, 0), cwo.ERR_INVALID_ARG),       # not a power of two
+    ((8192, 16, 1e-5, 1e-5, 633e-9, 0.1, 0, 0), cwo.ERR_INVALID_ARG),     # too large
+    ((16, 16, 0.0, 1e-5, 633e-9, 0.1, 0, 0), cwo.ERR_INVALID_ARG),        # zero pitch
+    ((16, 16, 1e-5, 1e-5, -1.0, 0.1, 0, 0), cwo.ERR_INVALID_ARG),         # negative wavelength
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.0, 1, 0), cwo.ERR_INVALID_ARG),       # Fresnel at z = 0
+    ((16, 16, 1e-5, 1e-5, 633e-9, float("nan"), 0, 0), cwo.ERR_INVALID_ARG),
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 2, 0), cwo.ERR_UNSUPPORTED),       # Fresnel Fourier form
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 3, 0), cwo.ERR_UNSUPPORTED),       # shifted Fresnel
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 4, 0), cwo.ERR_UNSUPPORTED),       # shifted ASM
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 9, 0), cwo.ERR_INVALID_ARG),       # unknown type
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 0, 0x80), cwo.ERR_INVALID_ARG),    # unknown flag
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 0, 3), cwo.ERR_INVALID_ARG),       # exclusive flags
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 1, 1), cwo.ERR_INVALID_ARG),       # phase flag on Fresnel
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 0, 4), cwo.ERR_INVALID_ARG),       # literal scale on ASM
+])
+def test_plan_create_rejects_bad_arguments_before_touching_a_device(lib, args, status):
+    h = ctypes.c_void_p(123)
+    st = lib.cwo_plan_create(*args, ctypes.byref(h))
+    assert st == status
+    assert not h.value
+    assert cwo.last_error()
+
+
+def test_null_arguments(lib):
+    assert lib.cwo_plan_create(16, 16, 1e-5, 1e-5, 633e-9, 0.1, 0, 0, None) == cwo.ERR_INVALID_ARG
+    assert lib.cwo_propagate(None, None, None, None) == cwo.ERR_INVALID_ARG
+    assert lib.cwo_plan_destroy(None) == cwo.OK
+    assert lib.cwo_plan_reserve(None, 1) == cwo.ERR_INVALID_ARG
+    assert lib.cwo_plan_device_bytes(16, 16, 1, None) == cwo.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("p", [32, 64, 128, 256, 512, 1024, 2048, 4096, 8192])
+def test_axis_bins_are_a_permutation_matching_the_line_fft(lib, p):
+    b = cwo.axis_bins(p)
+    assert sorted(b.tolist()) == list(range(p))
+    x = synth.random_field(p // 2, seed=p, ny=1)[0]
+    X = cwo.line_fft(x.astype(np.complex64))
+    ref = np.fft.fft(np.concatenate([x, np.zeros(p // 2)]))
+    assert np.linalg.norm(X - ref[b]) / np.linalg.norm(ref) < 5e-7
+    Y = synth.random_field(p, seed=p + 1, ny=1)[0]
+    y = cwo.line_fft(Y[b].astype(np.complex64), inverse=True)
+    want = (np.fft.ifft(Y) * p)[: p // 2]
+    assert np.linalg.norm(y - want) / np.linalg.norm(want) < 5e-7
+
+
+@pytest.mark.parametrize("p", [32, 256, 4096])
+def test_twiddle_tables(lib, p):
+    tw = cwo.twiddles(p)
+    T = p // 16
+    nst = (p.bit_length() - 1 + 3) // 4
+    L = p
+    for s in range(nst - 1):
+        S = L // 16
+        blk = tw[s * p:(s + 1) * p].reshape(16, T)
+        k = np.arange(16)[:, None]
+        t = np.arange(T)[None, :]
+        want = np.exp(-2j * np.pi * ((t % S) * k % L) / L)
+        assert np.max(np.abs(blk - want)) < 1e-7
+        L //= 16
+
+
+@pytest.mark.parametrize("p,pitch,lam,z", [(64, 10e-6, 633e-9, 0.05), (512, 8e-6, 532e-9, -0.3)])
+def test_fresnel_axis_dft(lib, p, pitch, lam, z):
+    d = np.where(np.arange(p) < p // 2, np.arange(p), np.arange(p) - p).astype(float)
+    h = np.exp(1j * np.pi * (d * pitch) ** 2 / (lam * z))
+    assert np.max(np.abs(cwo.fresnel_axis(p, pitch, lam, z) - np.fft.fft(h))) < 1e-9 * p
+
+
+
+@pytest.mark.parametrize("p,pitch,lam,z", [(8192, Decimal("3.74e-6"), Decimal("532e-9"), Decimal("1.0")),
+                                           (4096, Decimal("10e-6"), Decimal("633e-9"), Decimal("-0.2"))])
+def test_asm_axis_phase_reduction_is_exact(lib, p, pitch, lam, z):
+    # W = frac(K a/2 + K a^2/8) - frac(K) on x, recomputed with 50-digit decimals
+    getcontext().prec = 50
+    tab = cwo.asm_axis(p, float(pitch), float(lam), float(z), True)
+    bins = cwo.axis_bins(p)
+    K = z / lam
+    frK = K - (K.to_integral_value(rounding="ROUND_FLOOR"))
+    for i in list(range(0, p, p // 64)) + [p - 1]:
+        k = int(bins[i])
+        kt = k if k < p // 2 else k - p
+        a = lam * lam * Decimal(kt * kt) / (Decimal(p) * pitch) ** 2
+        ph = K * a / 2 + K * a * a / 8
+        W = ph - ph.to_integral_value(rounding="ROUND_FLOOR") - frK
+        got = Decimal(float(tab[i, 1]))
+        # compare modulo one cycle; float storage of a value in (-1, 1) is good to 6e-8
+        diff = (got - W) % 1
+        diff = min(diff, 1 - diff)
+        assert diff < Decimal("1.2e-7"), (i, kt, got, W)
+        assert abs(float(tab[i, 0]) - float(a)) <= 1e-7 * float(a) + 1e-30
+
+
+@pytest.mark.parametrize("nx,ny,kind,z,pitch", [
+    (16, 16, 0, 0.05, 10e-6), (32, 16, 0, 1e-3, 1e-6), (16, 64, 1, 0.02, 10e-6),
+    (64, 64, 1, 0.08, 8e-6), (64, 32, 0, 20e-6, 0.4e-6), (128, 128, 0, -0.1, 10e-6),
+])
+@pytest.mark.parametrize("adjoint", [0, 1])
+def test_host_emulation_of_the_kernels_matches_the_oracle(lib, nx, ny, kind, z, pitch, adjoint):
+    u = synth.random_field(nx, seed=nx + ny, ny=ny)
+    got = cwo.emulate(u.astype(np.complex64), pitch, pitch, 633e-9, z, kind, 0, adjoint)
+    want = oracle.propagate(u, pitch, pitch, 633e-9, z, kind, oracle.ADJOINT if adjoint else 0)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-5
