@@ -37,7 +37,7 @@ def _compile(src: str, verbose: bool) -> str:
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if src.endswith(".cu"):
         cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-               *inc, "-c", os.path.join(CSRC, src), "-o", obj]
+               *inc, *os.environ.get("CWO_EXTRA_NVCC_FLAGS", "").split(), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
     else:

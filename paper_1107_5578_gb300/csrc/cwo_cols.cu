@@ -2,8 +2,9 @@
 // inverse FFT, crop to the Ny source rows -- the "FFT", "multiply by H" and "IFFT" steps of
 // Eqs. ang3 / fre_conv_fft along y, fused in one kernel.
 //
-// Each column holds Ny stored rows; rows Ny .. Py-1 are the zero padding, seen as constant
-// zeros by the first DIF stage.  The forward transform ends in DIF (digit-reversed) order, the
+// The intermediate is column-major ([items][Px][Ny]), so each column is Ny contiguous complex64
+// values and every global access of this pass is a coalesced 256-byte warp transaction.  Rows
+// Ny .. Py-1 are the zero padding, seen as constant zeros by the first DIF stage.  The forward transform ends in DIF (digit-reversed) order, the
 // transfer function is generated for that order, and the inverse (the exact adjoint of the
 // forward stages) starts from it: no reordering and no exchange between the last forward and the
 // first inverse stage.  Only the Ny kept rows are written back.
@@ -22,13 +23,8 @@
 #include "cwo_internal.h"
 #include "cwo_h.cuh"
 
-namespace cwo {
 
-template <int P> constexpr int cols_per_block() {
-    constexpr int T = P / 16;
-    constexpr int c = 512 / T;
-    return c < 1 ? 1 : (c > 32 ? 32 : c);
-}
+namespace cwo {
 
 __device__ __forceinline__ float2 asm_h_fp32(int kbx, int kby, const HParams& hp) {
     // Eq. ang2 evaluated literally in single precision (precision-study arm)
@@ -43,91 +39,146 @@ __device__ __forceinline__ float2 asm_h_fp32(int kbx, int kby, const HParams& hp
     return make_float2(cs, sn);
 }
 
-__device__ __forceinline__ float2 asm_h_fp64(int kbx, int kby, const HParams& hp) {
-    // phase K sqrt(1 - s) per element in FP64, reduced to [-1/2, 1/2] cycle (reference arm)
-    const double s = hp.sx * (double)kbx * (double)kbx + hp.sy * (double)kby * (double)kby;
-    if (s > 1.0) return make_float2(0.f, 0.f);
-    double psi = hp.K * sqrt(1.0 - s);
-    psi -= rint(psi);
-    float sn, cs;
-    sincospif(2.0f * (float)psi, &sn, &cs);
-    return make_float2(cs, sn);
-}
-
-template <int P>
-__device__ __forceinline__ void apply_h(float2 (&v)[16], int col, int t, long long item,
+// multiply the registers of NV transforms of the same storage column pair (same |kx|) by H
+template <int P, int NV>
+__device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int col, int t, long long item,
                                         const HParams& hp) {
     constexpr int T = P / 16;
+    auto mul = [&](int e, float2 h) {
+        a[e] = hp.conj ? cmulc(a[e], h) : cmul(a[e], h);
+        if (NV == 2) b[e] = hp.conj ? cmulc(b[e], h) : cmul(b[e], h);
+    };
     if (hp.mode == HMODE_FRESNEL) {
         const float2 hxc = __ldg(hp.hx + item * hp.x_item_stride + col);
         const float2* hy = hp.hy + item * hp.y_item_stride + t;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const float2 h = cmul(hxc, __ldg(hy + e * T));
-            v[e] = hp.conj ? cmulc(v[e], h) : cmul(v[e], h);
-        }
-    } else if (hp.mode == HMODE_ASM_REDUCED) {
+        for (int e = 0; e < 16; ++e) mul(e, cmul(hxc, __ldg(hy + e * T)));
+    } else if (hp.mode == HMODE_ASM_POLY || hp.mode == HMODE_ASM_EXACT) {
         const float4 X = __ldg(hp.ax + item * hp.x_item_stride + col);
         const float4* ay = hp.ay + item * hp.y_item_stride + t;
         const float K = __ldg(hp.kf + item * hp.kf_item_stride);
+        if (hp.mode == HMODE_ASM_POLY) {
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const float2 h = asm_h_reduced(X, __ldg(ay + e * T), K);
-            v[e] = hp.conj ? cmulc(v[e], h) : cmul(v[e], h);
+            for (int e = 0; e < 16; ++e) mul(e, asm_h_reduced<true>(X, __ldg(ay + e * T), K));
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) mul(e, asm_h_reduced<false>(X, __ldg(ay + e * T), K));
         }
     } else {
         const int kbx = __ldg(hp.kbx + col);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
             const int kby = __ldg(hp.kby + e * T + t);
-            const float2 h = hp.mode == HMODE_ASM_FP32 ? asm_h_fp32(kbx, kby, hp) : asm_h_fp64(kbx, kby, hp);
-            v[e] = hp.conj ? cmulc(v[e], h) : cmul(v[e], h);
+            mul(e, hp.mode == HMODE_ASM_FP32 ? asm_h_fp32(kbx, kby, hp) : asm_h_fp64(kbx, kby, hp.K, hp.sx, hp.sy));
         }
     }
 }
 
-template <int P, int C>
-__global__ void __launch_bounds__(C * (P / 16))
-k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
-      long long wout_item_stride, int px, const float2* __restrict__ tw, const HParams hp) {
+// columns per block (single-column kernel) and mirror pairs per block (paired kernel)
+template <int P> constexpr int cols_per_block() {
     constexpr int T = P / 16;
+    constexpr int c = 256 / T;
+    return c < 1 ? 1 : (c > 16 ? 16 : c);
+}
+template <int P> constexpr int col_min_blocks() { return (P / 16) * cols_per_block<P>() <= 256 ? 2 : 1; }
+// the paired kernel holds 32 values per thread; above P = 4096 it would need more than the 128
+// registers two resident CTAs allow, so the largest size uses the single-column kernel
+template <int P> constexpr bool col_paired() { return P <= 4096; }
+
+// single column per transform (used where the paired kernel would not fit in registers)
+template <int P, int C>
+__global__ void __launch_bounds__(C * (P / 16), col_min_blocks<P>())
+k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
+      long long wout_item_stride, const float4* __restrict__ tw, const HParams hp) {
+    constexpr int T = P / 16, NY = P / 2;
+    using Lay = PadLayout<P, C>;
     extern __shared__ float2 sm[];
-    const int c = threadIdx.x % C, t = threadIdx.x / C;
+    const int t = threadIdx.x % T, c = threadIdx.x / T;
     const int col = blockIdx.x * C + c;
     const long long item = blockIdx.y;
-    const float2* src = win + item * win_item_stride + col;
+    const float2* src = win + item * win_item_stride + (long long)col * NY;
     float2 v[16];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = src[(long long)(t + e * T) * px];   // rows < Ny only
+    for (int e = 0; e < 8; ++e) v[e] = src[t + e * T];           // rows t + e P/16 < Ny
 #pragma unroll
-    for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);
-    fwd_from<P, C, 0, 8>(v, sm, c, t, tw);
-    apply_h<P>(v, col, t, item, hp);
-    inv_from<P, C, Geo<P>::NST - 1>(v, sm, c, t, tw);
-    float2* dst = wout + item * wout_item_stride + col;
+    for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);   // zero padding rows
+    const TwTable<P> twt{tw, t};
+    fwd_from<P, C, Lay, 0, 8, 0>(v, sm, c, t, twt);
+    apply_h<P, 1>(v, v, col, t, item, hp);
+    inv_from<P, C, Lay, Geo<P>::NST - 1, 0, 0>(v, sm, c, t, twt);
+    float2* dst = wout + item * wout_item_stride + (long long)col * NY;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) dst[(long long)(t + e * T) * px] = v[e];   // crop: rows < Ny
+    for (int e = 0; e < 8; ++e) dst[t + e * T] = v[e];           // crop: rows < Ny
+}
+
+// Mirror-pair column kernel: a thread transforms the two storage columns of frequencies +kx and
+// -kx.  H depends on kx only through kx^2 (both methods), so the transfer function is evaluated
+// once for both, and the twiddles of each stage are loaded once for both.
+template <int P, int CP>
+__global__ void __launch_bounds__(CP * (P / 16), 2)
+k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
+       long long wout_item_stride, const float4* __restrict__ tw, const HParams hp) {
+    constexpr int T = P / 16, NY = P / 2;
+    using Lay = PadLayout<P, 2 * CP>;
+    extern __shared__ float2 sm[];
+    const int t = threadIdx.x % T, cp = threadIdx.x / T;
+    const int j = blockIdx.x * CP + cp;
+    const bool live = j < hp.npairs;               // padding pairs of the last block compute, never store
+    const int2 pr = __ldg(hp.pairs + (live ? j : 0));
+    const long long item = blockIdx.y;
+    const float2* sa = win + item * win_item_stride + (long long)pr.x * NY;
+    const float2* sb = win + item * win_item_stride + (long long)pr.y * NY;
+    float2 a[16], b[16];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) { a[e] = sa[t + e * T]; b[e] = sb[t + e * T]; }
+#pragma unroll
+    for (int e = 8; e < 16; ++e) { a[e] = make_float2(0.f, 0.f); b[e] = make_float2(0.f, 0.f); }
+    fwd2_from<P, 2 * CP, Lay, 0, 8, 0>(a, b, sm, 2 * cp, t, tw);
+    apply_h<P, 2>(a, b, pr.x, t, item, hp);
+    inv2_from<P, 2 * CP, Lay, Geo<P>::NST - 1, 0, 0>(a, b, sm, 2 * cp, t, tw);
+    if (live) {
+        float2* da = wout + item * wout_item_stride + (long long)pr.x * NY;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) da[t + e * T] = a[e];
+        if (pr.y != pr.x) {                        // self-mirrored frequencies 0 and Px/2
+            float2* db = wout + item * wout_item_stride + (long long)pr.y * NY;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) db[t + e * T] = b[e];
+        }
+    }
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int P>
 static cudaError_t col_impl(const float2* win, long long win_item_stride, float2* wout,
-                            long long wout_item_stride, int px, int items, const float2* tw,
+                            long long wout_item_stride, int px, int items, const float4* tw,
                             const HParams& hp, cudaStream_t st) {
-    constexpr int C = cols_per_block<P>();
     constexpr int T = P / 16;
-    const size_t smem = (size_t)C * P * sizeof(float2);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_col<P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if constexpr (col_paired<P>()) {
+        constexpr int CP = cols_per_block<P>();
+        const size_t smem = (size_t)PadLayout<P, 2 * CP>::WORDS * sizeof(float2);
+        if ((e = set_smem(k_colp<P, CP>, smem))) return e;
+        if (hp.npairs != px / 2 + 1 || !hp.pairs) return cudaErrorInvalidValue;
+        const unsigned blocks = (unsigned)((hp.npairs + CP - 1) / CP);
+        k_colp<P, CP><<<dim3(blocks, items), CP * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
+    } else {
+        constexpr int C = cols_per_block<P>();
+        if (px % C != 0) return cudaErrorInvalidValue;
+        const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
+        if ((e = set_smem(k_col<P, C>, smem))) return e;
+        k_col<P, C><<<dim3(px / C, items), C * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
     }
-    if (px % C != 0) return cudaErrorInvalidValue;
-    dim3 grid(px / C, items);
-    k_col<P, C><<<grid, C * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, px, tw, hp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_col(int py, const float2* win, long long win_item_stride, float2* wout,
-                       long long wout_item_stride, int px, int items, const float2* tw,
+                       long long wout_item_stride, int px, int items, const float4* tw,
                        const HParams& hp, cudaStream_t st) {
     switch (py) {
 #define CASE(P) case P: return col_impl<P>(win, win_item_stride, wout, wout_item_stride, px, items, tw, hp, st);

@@ -21,11 +21,12 @@ namespace {
 struct Regs { float2 v[16]; };
 
 template <int P, int S, bool INV>
-void emu_twiddle(std::vector<Regs>& R, const float2* tw) {
+void emu_twiddle(std::vector<Regs>& R, const float4* tw) {
     constexpr int T = Geo<P>::T;
     for (int t = 0; t < T; ++t)
         for (int k = 1; k < 16; ++k) {
-            const float2 w = tw[S * P + k * T + t];
+            const float4 q = tw[S * (P / 2) + ((k - 1) / 2) * T + t];
+            const float2 w = (k & 1) ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
             R[t].v[k] = INV ? cmulc(R[t].v[k], w) : cmul(R[t].v[k], w);
         }
 }
@@ -33,15 +34,15 @@ void emu_twiddle(std::vector<Regs>& R, const float2* tw) {
 template <int P, int SW, int SR>
 void emu_exchange(std::vector<Regs>& R) {
     constexpr int T = Geo<P>::T;
-    std::vector<float2> sm(P);
+    std::vector<float2> sm(PadLayout<P, 1>::WORDS);
     for (int t = 0; t < T; ++t)
-        for (int e = 0; e < 16; ++e) sm[swz<P, 1>(0, stage_pos<P, SW>(t, e))] = R[t].v[e];
+        for (int e = 0; e < 16; ++e) sm[PadLayout<P, 1>::addr(0, stage_pos<P, SW>(t, e))] = R[t].v[e];
     for (int t = 0; t < T; ++t)
-        for (int e = 0; e < 16; ++e) R[t].v[e] = sm[swz<P, 1>(0, stage_pos<P, SR>(t, e))];
+        for (int e = 0; e < 16; ++e) R[t].v[e] = sm[PadLayout<P, 1>::addr(0, stage_pos<P, SR>(t, e))];
 }
 
 template <int P, int S, int NZ0>
-void emu_fwd_from(std::vector<Regs>& R, const float2* tw) {
+void emu_fwd_from(std::vector<Regs>& R, const float4* tw) {
     using G = Geo<P>;
     for (int t = 0; t < G::T; ++t) stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(R[t].v);
     if constexpr (S < G::NST - 1) {
@@ -52,7 +53,7 @@ void emu_fwd_from(std::vector<Regs>& R, const float2* tw) {
 }
 
 template <int P, int S>
-void emu_inv_from(std::vector<Regs>& R, const float2* tw) {
+void emu_inv_from(std::vector<Regs>& R, const float4* tw) {
     using G = Geo<P>;
     if constexpr (S < G::NST - 1) emu_twiddle<P, S, true>(R, tw);
     for (int t = 0; t < G::T; ++t) stage_butterflies<P, S, true, 16>(R[t].v);
@@ -64,7 +65,7 @@ void emu_inv_from(std::vector<Regs>& R, const float2* tw) {
 
 // forward transform of one padded line: in[0..P/2) nonzero; out in axis-index order
 template <int P>
-void emu_line_fwd(const float2* in, long long in_step, float2* out, long long out_step, const float2* tw) {
+void emu_line_fwd(const float2* in, long long in_step, float2* out, long long out_step, const float4* tw) {
     constexpr int T = P / 16;
     std::vector<Regs> R(T);
     for (int t = 0; t < T; ++t)
@@ -77,7 +78,7 @@ void emu_line_fwd(const float2* in, long long in_step, float2* out, long long ou
 
 // adjoint transform of one line given in axis-index order; keeps the first P/2 outputs
 template <int P>
-void emu_line_inv(const float2* in, long long in_step, float2* out, long long out_step, const float2* tw) {
+void emu_line_inv(const float2* in, long long in_step, float2* out, long long out_step, const float4* tw) {
     constexpr int T = P / 16;
     std::vector<Regs> R(T);
     for (int t = 0; t < T; ++t)
@@ -87,7 +88,7 @@ void emu_line_inv(const float2* in, long long in_step, float2* out, long long ou
         for (int e = 0; e < 8; ++e) out[(long long)(t + e * T) * out_step] = R[t].v[e];
 }
 
-using LineFn = void (*)(const float2*, long long, float2*, long long, const float2*);
+using LineFn = void (*)(const float2*, long long, float2*, long long, const float4*);
 
 LineFn pick_fwd(int p) {
     switch (p) {
@@ -120,13 +121,18 @@ extern "C" cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, do
         return CWO_ERR_INVALID_ARG;
     const int px = 2 * nx, py = 2 * ny;
     const AxisGeo gx(px), gy(py);
-    const std::vector<float2> twx = twiddle_table(gx), twy = twiddle_table(gy);
+    const std::vector<float4> twx = twiddle_table(gx), twy = twiddle_table(gy);
     std::vector<float4> ax(px), ay(py);
     std::vector<float2> hx(px), hy(py);
     float K = 0.f;
     const bool fresnel = type == CWO_FRESNEL_CONV;
     make_h_tables(px, py, dx, dy, lambda, z, fresnel, (flags & CWO_FLAG_LITERAL_SCALE) != 0,
                   ax.data(), ay.data(), hx.data(), hy.data(), &K);
+    const int tmode = asm_tail_mode(px, py, dx, dy, lambda, z);
+    const bool poly = tmode == 0;
+    const std::vector<int> kbx = bin_table(gx), kby = bin_table(gy);
+    const double sx = lambda * lambda / ((double)px * dx * (double)px * dx);
+    const double sy = lambda * lambda / ((double)py * dy * (double)py * dy);
     const float2* in = (const float2*)in_ri;
     float2* out = (float2*)out_ri;
     std::vector<float2> W((size_t)ny * px);
@@ -136,7 +142,10 @@ extern "C" cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, do
     for (int c = 0; c < px; ++c) {
         fy(W.data() + c, px, col.data(), 1, twy.data());
         for (int i = 0; i < py; ++i) {
-            float2 h = fresnel ? cmul(hx[c], hy[i]) : asm_h_reduced(ax[c], ay[i], K);
+            float2 h;
+            if (fresnel) h = cmul(hx[c], hy[i]);
+            else if (tmode == 2) h = asm_h_fp64(kbx[c], kby[i], z / lambda, sx, sy);
+            else h = poly ? asm_h_reduced<true>(ax[c], ay[i], K) : asm_h_reduced<false>(ax[c], ay[i], K);
             col[i] = adjoint ? cmulc(col[i], h) : cmul(col[i], h);
         }
         iy(col.data(), 1, W.data() + c, px, twy.data());
@@ -155,7 +164,7 @@ extern "C" cwo_status cwo_debug_line_fft(int p, int inverse, const float* in_ri,
     using namespace cwo::host;
     if (!in_ri || !out_ri || p < 32 || p > 8192 || (p & (p - 1))) return CWO_ERR_INVALID_ARG;
     const AxisGeo g(p);
-    const std::vector<float2> tw = twiddle_table(g);
+    const std::vector<float4> tw = twiddle_table(g);
     if (!inverse) pick_fwd(p)((const float2*)in_ri, 1, (float2*)out_ri, 1, tw.data());
     else pick_inv(p)((const float2*)in_ri, 1, (float2*)out_ri, 1, tw.data());
     return CWO_OK;

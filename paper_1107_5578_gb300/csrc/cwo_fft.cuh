@@ -183,60 +183,194 @@ CWO_HD int stage_pos(int t, int e) {
     }
 }
 
-// shared-memory word of position pos of transform c (C transforms per block)
+// Shared-memory layouts of C transforms of length P.  Both keep every access of every stage
+// bank-conflict free when the C transforms are interleaved across a warp's lanes.
+//   SwzLayout: XOR swizzle of the low 4 position bits (no padding).
+//   PadLayout: one pad word per 16 positions plus a per-transform shift of 16/C words; the
+//              address of register e at any stage is a per-thread base plus a compile-time
+//              constant, so no per-element address arithmetic is left.
 template <int P, int C>
 CWO_HD int swz(int c, int pos) {
     constexpr int K = C >= 16 ? 1 : 16 / C;
     return c * P + (pos ^ (((pos >> 4) ^ (c * K)) & 15));
 }
+template <int P, int C>
+struct SwzLayout {
+    static constexpr int WORDS = C * P;
+    static CWO_HD int addr(int c, int pos) { return swz<P, C>(c, pos); }
+};
+template <int P, int C>
+struct PadLayout {
+    static constexpr int R = P + P / 16 + (C <= 16 ? 16 / C : 1);
+    static constexpr int WORDS = C * R;
+    static CWO_HD int addr(int c, int pos) { return c * R + pos + (pos >> 4); }
+};
+
+// Tile of R rows x P storage columns used to transpose between the row passes and the
+// column-major intermediate: linear index st * R + r plus one pad word per 16, which keeps both
+// the per-row access (lanes over st) and the per-column access (lanes over r, then st) free of
+// bank conflicts.
+template <int P, int R>
+struct TileLayout {
+    static constexpr int WORDS = P * R + (P * R) / 16;
+    static CWO_HD int addr(int st, int r) { const int i = st * R + r; return i + (i >> 4); }
+};
 
 #ifdef __CUDACC__
-// write the registers at the positions of stage SW, read them back at the positions of stage SR
-template <int P, int C, int SW, int SR>
+// Write the registers at the positions of stage SW, read them back at the positions of stage SR.
+// PING = 0: one buffer, a barrier after the write and another after the read.
+// PING = 1: exchange number XNUM uses buffer XNUM % 2 of two consecutive buffers and needs no
+//           trailing barrier (a buffer is rewritten only two exchanges later, after every
+//           thread has passed the barrier of the exchange in between).
+template <int P, int C, class Lay, int SW, int SR, int PING, int XNUM>
 __device__ __forceinline__ void exchange(float2* __restrict__ sm, int c, int t, float2 (&v)[16]) {
+    float2* b = PING ? sm + (XNUM & 1) * Lay::WORDS : sm;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) sm[swz<P, C>(c, stage_pos<P, SW>(t, e))] = v[e];
+    for (int e = 0; e < 16; ++e) b[Lay::addr(c, stage_pos<P, SW>(t, e))] = v[e];
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = sm[swz<P, C>(c, stage_pos<P, SR>(t, e))];
-    __syncthreads();
+    for (int e = 0; e < 16; ++e) v[e] = b[Lay::addr(c, stage_pos<P, SR>(t, e))];
+    if (!PING) __syncthreads();
 }
 
-// inter-stage twiddles of stage S (< NST-1): table block S holds W_{L_S}^{(t % S_S) k'} at [k'][t]
-template <int P, int S, bool INV>
-__device__ __forceinline__ void stage_twiddle(float2 (&v)[16], int t, const float2* __restrict__ tw) {
-    constexpr int T = Geo<P>::T;
-    const float2* base = tw + S * P + t;
+// Inter-stage twiddles W_{L_s}^{(t % S_s) k'}, k' = 1..15, of stage s < NST-1.
+// TwTable: per stage a block of P/2 float4 laid out [kp][t], kp = 0..7, holding the pair
+//          (W^{j (2kp+1)}, W^{j (2kp+2)}): 8 coalesced 16-byte loads per thread and stage.
+template <int P>
+struct TwTable {
+    const float4* __restrict__ tw;
+    int t;
+    template <int S, bool INV>
+    __device__ __forceinline__ void apply(float2 (&v)[16]) const {
+        constexpr int T = Geo<P>::T;
+        const float4* base = tw + S * (P / 2) + t;
 #pragma unroll
-    for (int k = 1; k < 16; ++k) {
-        float2 w = __ldg(base + k * T);
-        v[k] = INV ? cmulc(v[k], w) : cmul(v[k], w);
+        for (int kp = 0; kp < 8; ++kp) {
+            const float4 w = __ldg(base + kp * T);
+            v[2 * kp + 1] = INV ? cmulc(v[2 * kp + 1], make_float2(w.x, w.y)) : cmul(v[2 * kp + 1], make_float2(w.x, w.y));
+            if (kp < 7)
+                v[2 * kp + 2] = INV ? cmulc(v[2 * kp + 2], make_float2(w.z, w.w)) : cmul(v[2 * kp + 2], make_float2(w.z, w.w));
+        }
+    }
+};
+
+// the same twiddles applied to two transforms held by the same thread (two columns)
+template <int P, int S, bool INV>
+__device__ __forceinline__ void twiddle2(float2 (&a)[16], float2 (&b)[16], const float4* __restrict__ tw, int t) {
+    constexpr int T = Geo<P>::T;
+    const float4* base = tw + S * (P / 2) + t;
+#pragma unroll
+    for (int kp = 0; kp < 8; ++kp) {
+        const float4 w = __ldg(base + kp * T);
+        const float2 w0 = make_float2(w.x, w.y), w1 = make_float2(w.z, w.w);
+        a[2 * kp + 1] = INV ? cmulc(a[2 * kp + 1], w0) : cmul(a[2 * kp + 1], w0);
+        b[2 * kp + 1] = INV ? cmulc(b[2 * kp + 1], w0) : cmul(b[2 * kp + 1], w0);
+        if (kp < 7) {
+            a[2 * kp + 2] = INV ? cmulc(a[2 * kp + 2], w1) : cmul(a[2 * kp + 2], w1);
+            b[2 * kp + 2] = INV ? cmulc(b[2 * kp + 2], w1) : cmul(b[2 * kp + 2], w1);
+        }
+    }
+}
+
+// TwRegs: the twiddles of the first two stages held in registers for the life of a persistent
+// thread (they depend on t only), loaded once from the same table.
+template <int P>
+struct TwRegs {
+    static constexpr int NS = Geo<P>::NST - 1 < 2 ? Geo<P>::NST - 1 : 2;   // stages kept
+    float2 w[NS > 0 ? NS : 1][15];
+    const float4* __restrict__ tw;
+    int t;
+    __device__ __forceinline__ void load(const float4* __restrict__ table, int tt) {
+        tw = table;
+        t = tt;
+        constexpr int T = Geo<P>::T;
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int kp = 0; kp < 8; ++kp) {
+                const float4 q = __ldg(table + s * (P / 2) + kp * T + tt);
+                w[s][2 * kp] = make_float2(q.x, q.y);
+                if (kp < 7) w[s][2 * kp + 1] = make_float2(q.z, q.w);
+            }
+    }
+    template <int S, bool INV>
+    __device__ __forceinline__ void apply(float2 (&v)[16]) const {
+        if constexpr (S < NS) {
+#pragma unroll
+            for (int k = 1; k < 16; ++k) v[k] = INV ? cmulc(v[k], w[S][k - 1]) : cmul(v[k], w[S][k - 1]);
+        } else {
+            TwTable<P>{tw, t}.template apply<S, INV>(v);
+        }
+    }
+};
+
+// exchange of two transforms (indices c0, c0 + 1) held by the same thread
+template <int P, int C, class Lay, int SW, int SR, int PING, int XNUM>
+__device__ __forceinline__ void exchange2(float2* __restrict__ sm, int c0, int t, float2 (&a)[16], float2 (&b)[16]) {
+    float2* s = PING ? sm + (XNUM & 1) * Lay::WORDS : sm;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        s[Lay::addr(c0, stage_pos<P, SW>(t, e))] = a[e];
+        s[Lay::addr(c0 + 1, stage_pos<P, SW>(t, e))] = b[e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        a[e] = s[Lay::addr(c0, stage_pos<P, SR>(t, e))];
+        b[e] = s[Lay::addr(c0 + 1, stage_pos<P, SR>(t, e))];
+    }
+    if (!PING) __syncthreads();
+}
+
+// forward DIF of two transforms sharing thread, twiddles and exchanges
+template <int P, int C, class Lay, int S, int NZ0, int PING>
+__device__ __forceinline__ void fwd2_from(float2 (&a)[16], float2 (&b)[16], float2* __restrict__ sm, int c0, int t,
+                                          const float4* __restrict__ tw) {
+    using G = Geo<P>;
+    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(a);
+    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(b);
+    if constexpr (S < G::NST - 1) {
+        twiddle2<P, S, false>(a, b, tw, t);
+        exchange2<P, C, Lay, S, S + 1, PING, S>(sm, c0, t, a, b);
+        fwd2_from<P, C, Lay, S + 1, NZ0, PING>(a, b, sm, c0, t, tw);
+    }
+}
+
+template <int P, int C, class Lay, int S, int PING, int XOFF>
+__device__ __forceinline__ void inv2_from(float2 (&a)[16], float2 (&b)[16], float2* __restrict__ sm, int c0, int t,
+                                          const float4* __restrict__ tw) {
+    using G = Geo<P>;
+    if constexpr (S < G::NST - 1) twiddle2<P, S, true>(a, b, tw, t);
+    stage_butterflies<P, S, true, 16>(a);
+    stage_butterflies<P, S, true, 16>(b);
+    if constexpr (S > 0) {
+        exchange2<P, C, Lay, S, S - 1, PING, XOFF + (G::NST - 1 - S)>(sm, c0, t, a, b);
+        inv2_from<P, C, Lay, S - 1, PING, XOFF>(a, b, sm, c0, t, tw);
     }
 }
 
 // forward DIF from stage S to the end; the registers enter holding stage-S input positions
-template <int P, int C, int S, int NZ0>
-__device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ sm, int c, int t,
-                                         const float2* __restrict__ tw) {
+template <int P, int C, class Lay, int S, int NZ0, int PING, class Tw>
+__device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ sm, int c, int t, const Tw& tw) {
     using G = Geo<P>;
     stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(v);
     if constexpr (S < G::NST - 1) {
-        stage_twiddle<P, S, false>(v, t, tw);
-        exchange<P, C, S, S + 1>(sm, c, t, v);
-        fwd_from<P, C, S + 1, NZ0>(v, sm, c, t, tw);
+        tw.template apply<S, false>(v);
+        exchange<P, C, Lay, S, S + 1, PING, S>(sm, c, t, v);
+        fwd_from<P, C, Lay, S + 1, NZ0, PING>(v, sm, c, t, tw);
     }
 }
 
-// adjoint (inverse DIT) from stage S down to stage 0; the registers enter holding stage-S positions
-template <int P, int C, int S>
-__device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ sm, int c, int t,
-                                         const float2* __restrict__ tw) {
+// adjoint (inverse DIT) from stage S down to stage 0; the registers enter holding stage-S
+// positions.  XOFF numbers its exchanges after those of a preceding forward transform.
+template <int P, int C, class Lay, int S, int PING, int XOFF, class Tw>
+__device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ sm, int c, int t, const Tw& tw) {
     using G = Geo<P>;
-    if constexpr (S < G::NST - 1) stage_twiddle<P, S, true>(v, t, tw);
+    if constexpr (S < G::NST - 1) tw.template apply<S, true>(v);
     stage_butterflies<P, S, true, 16>(v);
     if constexpr (S > 0) {
-        exchange<P, C, S, S - 1>(sm, c, t, v);
-        inv_from<P, C, S - 1>(v, sm, c, t, tw);
+        exchange<P, C, Lay, S, S - 1, PING, XOFF + (G::NST - 1 - S)>(sm, c, t, v);
+        inv_from<P, C, Lay, S - 1, PING, XOFF>(v, sm, c, t, tw);
     }
 }
 

@@ -7,10 +7,11 @@
 namespace cwo {
 
 enum HMode : int {
-    HMODE_ASM_REDUCED = 0,   // ASM, FP64-reduced per-axis phase + float-float cross term
-    HMODE_ASM_FP32 = 1,      // ASM, whole phase in FP32 (precision-study arm)
-    HMODE_ASM_FP64 = 2,      // ASM, literal per-element FP64 phase (precision-study arm)
-    HMODE_FRESNEL = 3,       // Fresnel, separable table product
+    HMODE_ASM_POLY = 0,      // ASM, FP64-reduced per-axis phase, float-float cross, series tail
+    HMODE_ASM_EXACT = 1,     // ASM, as above with the closed-form tail (larger s)
+    HMODE_ASM_FP32 = 2,      // ASM, whole phase in FP32 (precision-study arm)
+    HMODE_ASM_FP64 = 3,      // ASM, literal per-element FP64 phase (reference arm, large K s^3)
+    HMODE_FRESNEL = 4,       // Fresnel, separable table product
 };
 
 // Transfer-function description for the column pass.  Per-axis tables are indexed by the axis
@@ -36,17 +37,21 @@ struct HParams {
     double dfx, dfy;          // frequency pitches 1 / (P dx), 1 / (P dy) (FP32 arm)
     const int* kbx;           // signed bin of each axis index (FP32 / FP64 arms)
     const int* kby;
+    // storage-column pairs (st(+kx), st(-kx)) for kx = 0 .. Px/2 (paired column kernel)
+    const int2* pairs;
+    int npairs;               // Px/2 + 1
 };
 
 // launchers (return cudaGetLastError() after the launch)
+// The intermediate is column-major: [items][Px][Ny] complex64 (see cwo_rows.cu).
 cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, float2* w,
-                           long long w_item_stride, int ny, int items, const float2* tw,
+                           long long w_item_stride, int ny, int items, const float4* tw,
                            cudaStream_t st);
 cudaError_t launch_row_inv(int px, const float2* w, long long w_item_stride, float2* out,
                            long long out_item_stride, int ny, int items, float scale,
-                           const float2* tw, cudaStream_t st);
+                           const float4* tw, cudaStream_t st);
 cudaError_t launch_col(int py, const float2* win, long long win_item_stride, float2* wout,
-                       long long wout_item_stride, int px, int items, const float2* tw,
+                       long long wout_item_stride, int px, int items, const float4* tw,
                        const HParams& hp, cudaStream_t st);
 
 }  // namespace cwo

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -109,7 +110,7 @@ cwo_status upload(T* dst, const std::vector<T>& src, const char* what) {
 size_t tables_bytes(int nx, int ny) {
     const AxisGeo gx(2 * nx), gy(2 * ny);
     size_t b = 0;
-    b += (size_t)std::max(gx.NST - 1, 0) * gx.P * sizeof(float2) + (size_t)std::max(gy.NST - 1, 0) * gy.P * sizeof(float2);
+    b += (size_t)std::max(gx.NST - 1, 0) * (gx.P / 2) * sizeof(float4) + (size_t)std::max(gy.NST - 1, 0) * (gy.P / 2) * sizeof(float4);
     b += (size_t)(gx.P + gy.P) * sizeof(int);
     b += (size_t)(gx.P + gy.P) * sizeof(float4) + sizeof(float) * 2;
     return b;
@@ -126,10 +127,11 @@ struct cwo_plan {
     cwo_type type = CWO_ANGULAR;
     unsigned flags = 0;
     int device = 0;
-    float2* tw_x = nullptr;   // twiddles along x (rows, length px)
-    float2* tw_y = nullptr;   // twiddles along y (columns, length py); aliases tw_x if px == py
+    float4* tw_x = nullptr;   // twiddles along x (rows, length px)
+    float4* tw_y = nullptr;   // twiddles along y (columns, length py); aliases tw_x if px == py
     int* kb_x = nullptr;
     int* kb_y = nullptr;
+    int2* pairs_x = nullptr;   // mirror storage-column pairs along x
     // tables of the plan's own z
     float4* ax = nullptr; float4* ay = nullptr;
     float2* hx = nullptr; float2* hy = nullptr;
@@ -154,7 +156,7 @@ void free_plan(cwo_plan* p) {
     if (!p) return;
     cudaFree(p->tw_x);
     if (p->tw_y != p->tw_x) cudaFree(p->tw_y);
-    cudaFree(p->kb_x); cudaFree(p->kb_y);
+    cudaFree(p->kb_x); cudaFree(p->kb_y); cudaFree(p->pairs_x);
     cudaFree(p->ax); cudaFree(p->ay); cudaFree(p->hx); cudaFree(p->hy); cudaFree(p->kf);
     cudaFree(p->zax); cudaFree(p->zay); cudaFree(p->zhx); cudaFree(p->zhy); cudaFree(p->zkf);
     if (p->zhost) cudaFreeHost(p->zhost);
@@ -273,6 +275,8 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     hp.conj = adjoint ? 1 : 0;
     hp.kbx = p->kb_x;
     hp.kby = p->kb_y;
+    hp.pairs = p->pairs_x;
+    hp.npairs = p->px / 2 + 1;
     const double K = p->z / p->lambda;
     hp.K = K;
     hp.sx = p->lambda * p->lambda / ((double)p->px * p->dx * (double)p->px * p->dx);
@@ -284,9 +288,17 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     if (p->type == CWO_FRESNEL_CONV) hp.mode = cwo::HMODE_FRESNEL;
     else if (p->flags & CWO_FLAG_PHASE_FP32) hp.mode = cwo::HMODE_ASM_FP32;
     else if (p->flags & CWO_FLAG_PHASE_FP64) hp.mode = cwo::HMODE_ASM_FP64;
-    else hp.mode = cwo::HMODE_ASM_REDUCED;
+    else {
+        // the cheapest per-element remainder evaluation that stays within its error budget
+        int tm = 0;
+        if (zs) for (int i = 0; i < batch; ++i) tm = std::max(tm, asm_tail_mode(p->px, p->py, p->dx, p->dy, p->lambda, zs[i]));
+        else tm = asm_tail_mode(p->px, p->py, p->dx, p->dy, p->lambda, p->z);
+        hp.mode = tm == 0 ? cwo::HMODE_ASM_POLY : tm == 1 ? cwo::HMODE_ASM_EXACT : cwo::HMODE_ASM_FP64;
+    }
+    // FP64 per element with per-item distances: one launch set per item, each with its own K
+    const bool per_item_k = zs && hp.mode == cwo::HMODE_ASM_FP64;
 
-    if (zs) {
+    if (zs && !per_item_k) {
         if ((st = ensure_ztables(p, batch))) return st;
         if (p->zev_pending) {   // the staging buffer may still feed the previous upload
             cudaError_t e = cudaEventSynchronize(p->zev);
@@ -340,16 +352,33 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         float2* wz = p->scratch + wstride;
         if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, 0, w0, 0, p->ny, 1, p->tw_x, s)) || (e = mark(1)))
             return cuda_fail(e, "row forward launch");
-        if ((e = cwo::launch_col(p->py, w0, 0, wz, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2)))
+        if (per_item_k) {
+            for (int i = 0; i < batch; ++i) {
+                hp.K = zs[i] / p->lambda;
+                if ((e = cwo::launch_col(p->py, w0, 0, wz + i * wstride, 0, p->px, 1, p->tw_y, hp, s)))
+                    return cuda_fail(e, "column launch");
+            }
+            if ((e = mark(2))) return cuda_fail(e, "event");
+        } else if ((e = cwo::launch_col(p->py, w0, 0, wz, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2))) {
             return cuda_fail(e, "column launch");
+        }
         if ((e = cwo::launch_row_inv(p->px, wz, wstride, fout, field, p->ny, batch, scale, p->tw_x, s)) || (e = mark(3)))
             return cuda_fail(e, "row inverse launch");
     } else {
         const long long istr = in_stride ? in_stride : field;
         if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, istr, p->scratch, wstride, p->ny, batch, p->tw_x, s)) || (e = mark(1)))
             return cuda_fail(e, "row forward launch");
-        if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2)))
+        if (per_item_k) {
+            for (int i = 0; i < batch; ++i) {
+                hp.K = zs[i] / p->lambda;
+                float2* wi = p->scratch + i * wstride;
+                if ((e = cwo::launch_col(p->py, wi, 0, wi, 0, p->px, 1, p->tw_y, hp, s)))
+                    return cuda_fail(e, "column launch");
+            }
+            if ((e = mark(2))) return cuda_fail(e, "event");
+        } else if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2))) {
             return cuda_fail(e, "column launch");
+        }
         if ((e = cwo::launch_row_inv(p->px, p->scratch, wstride, fout, field, p->ny, batch, scale, p->tw_x, s)) || (e = mark(3)))
             return cuda_fail(e, "row inverse launch");
     }
@@ -389,15 +418,17 @@ cwo_status cwo_plan_create(int nx, int ny, double dx, double dy, double lambda, 
     if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaGetDevice"); }
 
     const AxisGeo gx(p->px), gy(p->py);
-    const std::vector<float2> twx = twiddle_table(gx);
+    const std::vector<float4> twx = twiddle_table(gx);
     const std::vector<int> kbx = bin_table(gx), kby = bin_table(gy);
     if ((st = dev_alloc(&p->tw_x, twx.size(), "x twiddles")) || (st = upload(p->tw_x, twx, "x twiddle upload"))) { free_plan(p); return st; }
     if (p->py == p->px) {
         p->tw_y = p->tw_x;
     } else {
-        const std::vector<float2> twy = twiddle_table(gy);
+        const std::vector<float4> twy = twiddle_table(gy);
         if ((st = dev_alloc(&p->tw_y, twy.size(), "y twiddles")) || (st = upload(p->tw_y, twy, "y twiddle upload"))) { free_plan(p); return st; }
     }
+    const std::vector<int2> prs = mirror_pairs(gx);
+    if ((st = dev_alloc(&p->pairs_x, prs.size(), "x pairs")) || (st = upload(p->pairs_x, prs, "x pair upload"))) { free_plan(p); return st; }
     if ((st = dev_alloc(&p->kb_x, kbx.size(), "x bins")) || (st = upload(p->kb_x, kbx, "x bin upload")) ||
         (st = dev_alloc(&p->kb_y, kby.size(), "y bins")) || (st = upload(p->kb_y, kby, "y bin upload"))) { free_plan(p); return st; }
     if (type == CWO_ANGULAR) {
@@ -482,8 +513,10 @@ cwo_status cwo_debug_fresnel_axis(int p, double pitch, double lambda, double z, 
 cwo_status cwo_debug_twiddles(int p, float* out_ri) {
     if (!out_ri || p < 32 || p > 8192 || (p & (p - 1))) return fail(CWO_ERR_INVALID_ARG, "bad axis length");
     const AxisGeo g(p);
-    const std::vector<float2> tw = twiddle_table(g);
-    for (size_t i = 0; i < tw.size(); ++i) { out_ri[2 * i] = tw[i].x; out_ri[2 * i + 1] = tw[i].y; }
+    const std::vector<float4> tw = twiddle_table(g);
+    for (size_t i = 0; i < tw.size(); ++i) {
+        out_ri[4 * i] = tw[i].x; out_ri[4 * i + 1] = tw[i].y; out_ri[4 * i + 2] = tw[i].z; out_ri[4 * i + 3] = tw[i].w;
+    }
     return CWO_OK;
 }
 

@@ -10,6 +10,7 @@
 //    reduced modulo one cycle in FP64 (see cwo_h.cuh for the split).
 #include "cwo_tables.h"
 
+#include <algorithm>
 #include <cmath>
 
 #include "../../include/cwo.h"
@@ -43,18 +44,35 @@ int AxisGeo::freq_of_pos(int pos) const {
     return k;
 }
 
-std::vector<float2> twiddle_table(const AxisGeo& g) {
-    std::vector<float2> tw((size_t)(g.NST > 1 ? g.NST - 1 : 0) * g.P);
+std::vector<float4> twiddle_table(const AxisGeo& g) {
+    // per radix-16 stage s: P/2 float4 laid out [kp][t], kp = 0..7, holding
+    // (W_L^{j (2kp+1)}, W_L^{j (2kp+2)}), j = t mod S_s, L = L_s
+    std::vector<float4> tw((size_t)(g.NST > 1 ? g.NST - 1 : 0) * (g.P / 2));
     for (int s = 0; s + 1 < g.NST; ++s) {
         const int L = g.len(s), S = g.stride(s);
-        for (int k = 0; k < 16; ++k)
+        for (int kp = 0; kp < 8; ++kp)
             for (int t = 0; t < g.T; ++t) {
-                const long long jk = (long long)(t % S) * k % L;
-                const double ang = -2.0 * kPi * (double)jk / (double)L;
-                tw[(size_t)s * g.P + (size_t)k * g.T + t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+                double re[2], im[2];
+                for (int h = 0; h < 2; ++h) {
+                    const long long jk = (long long)(t % S) * (2 * kp + 1 + h) % L;
+                    const double ang = -2.0 * kPi * (double)jk / (double)L;
+                    re[h] = std::cos(ang);
+                    im[h] = std::sin(ang);
+                }
+                tw[(size_t)s * (g.P / 2) + (size_t)kp * g.T + t] =
+                    make_float4((float)re[0], (float)im[0], (float)re[1], (float)im[1]);
             }
     }
     return tw;
+}
+
+std::vector<int2> mirror_pairs(const AxisGeo& g) {
+    std::vector<int> where(g.P);
+    for (int i = 0; i < g.P; ++i) where[g.freq_of_idx(i)] = i;
+    std::vector<int2> pr;
+    pr.reserve(g.P / 2 + 1);
+    for (int k = 0; k <= g.P / 2; ++k) pr.push_back(make_int2(where[k], where[(g.P - k) % g.P]));
+    return pr;
 }
 
 std::vector<int> bin_table(const AxisGeo& g) {
@@ -120,6 +138,19 @@ void asm_axis_table(const AxisGeo& g, double pitch, double lambda, double z, boo
     }
 }
 
+int asm_tail_mode(int px, int py, double dx, double dy, double lambda, double z) {
+    (void)px; (void)py;
+    const double K = std::fabs(z / lambda);
+    const double smax = lambda * lambda * (0.25 / (dx * dx) + 0.25 / (dy * dy));
+    if (smax < 0.5 && K * (429.0 / 32768.0) * std::pow(smax, 8) / (1.0 - smax) < 1e-8) return 0;
+    if (smax <= 1.0) {
+        const double q = std::sqrt(1.0 - smax), d = 1.0 + q;
+        const double tail = K * smax * smax * smax * (3.0 + q) / (8.0 * d * d * d);
+        if (tail <= 4.0) return 1;
+    }
+    return 2;
+}
+
 void make_h_tables(int px, int py, double dx, double dy, double lambda, double z, bool fresnel,
                    bool literal_scale, float4* ax, float4* ay, float2* hx, float2* hy, float* kf) {
     const AxisGeo gx(px), gy(py);
@@ -131,12 +162,16 @@ void make_h_tables(int px, int py, double dx, double dy, double lambda, double z
         const std::vector<cd> Hx = fresnel_axis_dft(px, dx, lambda, z);
         const std::vector<cd> Hy = fresnel_axis_dft(py, dy, lambda, z);
         const cd C = fresnel_coeff(dx, dy, lambda, z, literal_scale);
+        // h_F is even in d (the unpaired sample d = -P/2 contributes (-1)^k, also even), so
+        // H[k] = H[P - k]; one representative per pair keeps the float tables exactly even
         for (int i = 0; i < px; ++i) {
-            const cd v = C * Hx[gx.freq_of_idx(i)];
+            const int k = gx.freq_of_idx(i);
+            const cd v = C * Hx[std::min(k, (px - k) % px)];
             hx[i] = make_float2((float)v.real(), (float)v.imag());
         }
         for (int i = 0; i < py; ++i) {
-            const cd v = Hy[gy.freq_of_idx(i)];
+            const int k = gy.freq_of_idx(i);
+            const cd v = Hy[std::min(k, (py - k) % py)];
             hy[i] = make_float2((float)v.real(), (float)v.imag());
         }
     }

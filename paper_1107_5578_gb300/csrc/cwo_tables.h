@@ -24,8 +24,10 @@ struct AxisGeo {
 };
 
 double frac01(double x);
-std::vector<float2> twiddle_table(const AxisGeo& g);
+std::vector<float4> twiddle_table(const AxisGeo& g);
 std::vector<int> bin_table(const AxisGeo& g);
+// storage columns of the frequencies +k and -k for k = 0 .. P/2 (0 and P/2 pair with themselves)
+std::vector<int2> mirror_pairs(const AxisGeo& g);
 void fft64(std::vector<cd>& x);
 std::vector<cd> fresnel_axis_dft(int P, double pitch, double lambda, double z);
 cd fresnel_coeff(double dx, double dy, double lambda, double z, bool literal_scale);
@@ -37,6 +39,12 @@ struct HTables {
     std::vector<float2> hx, hy;   // Fresnel (hx includes C)
     float K = 0.f;                // z / lambda (angular spectrum tail term)
 };
+// Which per-element evaluation of the ASM phase remainder a parameter set needs:
+// 0 series tail (truncation < 1e-8 cycle), 1 closed-form tail (tail < 4 cycles, FP32 error
+// < 1e-6 cycle), 2 FP64 per element.  s_max = lambda^2 (1/(4 dx^2) + 1/(4 dy^2)) at the Nyquist
+// corner of the padded grid.
+int asm_tail_mode(int px, int py, double dx, double dy, double lambda, double z);
+
 void make_h_tables(int px, int py, double dx, double dy, double lambda, double z, bool fresnel,
                    bool literal_scale, float4* ax, float4* ay, float2* hx, float2* hy, float* kf);
 

@@ -102,19 +102,20 @@ def test_axis_bins_are_a_permutation_matching_the_line_fft(lib, p):
     assert np.linalg.norm(y - want) / np.linalg.norm(want) < 5e-7
 
 
-@pytest.mark.parametrize("p", [32, 256, 4096])
+@pytest.mark.parametrize("p", [32, 256, 4096, 8192])
 def test_twiddle_tables(lib, p):
-    tw = cwo.twiddles(p)
+    tw = cwo.twiddles(p)          # complex64 view: per stage [kp][t] pairs (k = 2kp+1, 2kp+2)
     T = p // 16
     nst = (p.bit_length() - 1 + 3) // 4
     L = p
     for s in range(nst - 1):
         S = L // 16
-        blk = tw[s * p:(s + 1) * p].reshape(16, T)
-        k = np.arange(16)[:, None]
+        blk = tw[s * p:(s + 1) * p].reshape(8, T, 2)
         t = np.arange(T)[None, :]
-        want = np.exp(-2j * np.pi * ((t % S) * k % L) / L)
-        assert np.max(np.abs(blk - want)) < 1e-7
+        for h in range(2):
+            k = (2 * np.arange(8) + 1 + h)[:, None]
+            want = np.exp(-2j * np.pi * ((t % S) * k % L) / L)
+            assert np.max(np.abs(blk[:, :, h] - want)) < 1e-7
         L //= 16
 
 
