@@ -151,6 +151,30 @@ int cwo_launches_per_call(const cwo_plan* plan);
  * cudaEventElapsedTime.  NULL switches recording off.  The caller keeps ownership of the events. */
 cwo_status cwo_plan_set_timing_events(cwo_plan* plan, void* const* events);
 
+/*
+ * Angular-spectrum propagation of one [ny][nx] complex64 field that allocates no memory.
+ * The paper has no counterpart: this serves callers that cannot allocate device memory when
+ * they propagate -- a host that has given the device to its own allocator and forbids side
+ * allocations, a real-time loop that must not risk the device synchronisation cudaMalloc can
+ * imply, or code running where no allocator is available.  The caller passes only the input and
+ * output fields (device memory of the current device; they may alias); the intermediate and the
+ * tables live in file-scope device arrays of this library, which every GPU that loads it keeps
+ * until the process exits.  Same method, conventions and accuracy as cwo_propagate with a
+ * CWO_ANGULAR plan.
+ *   limits   nx, ny powers of two in [16, 1024] (the fixed scratch is 1024 x 2048 complex64,
+ *            16 MiB); larger fields return CWO_ERR_INVALID_ARG without launching anything
+ *   set-up   the first call on a device, with that device current, resolves the arrays'
+ *            device addresses (cudaGetSymbolAddress); make that first call before any stream
+ *            capture
+ *   sharing  all calls use the same arrays, which keep the last call's contents; calls whose
+ *            work overlaps on the GPU (other streams or host threads) race and corrupt each
+ *            other.  Nothing has to start at zero: each call regenerates every table entry and
+ *            writes every intermediate element before it is read.
+ *   ordering enqueued on cuda_stream; no host synchronisation; allocates nothing.
+ */
+cwo_status cwo_propagate_asm_noalloc(int nx, int ny, double dx, double dy, double lambda, double z,
+                                     const void* in_c64, void* out_c64, void* cuda_stream);
+
 /* Thread-local description of the most recent failure on this thread ("" if none). */
 const char* cwo_last_error(void);
 

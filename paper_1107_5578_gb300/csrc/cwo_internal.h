@@ -43,6 +43,9 @@ struct HParams {
 };
 
 // launchers (return cudaGetLastError() after the launch)
+// Record the message returned by cwo_last_error() on this thread.
+void set_last_error(const char* msg);
+
 // The intermediate is column-major: [items][Px][Ny] complex64 (see cwo_rows.cu).
 cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, float2* w,
                            long long w_item_stride, int ny, int items, const float4* tw,

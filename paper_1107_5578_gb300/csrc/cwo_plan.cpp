@@ -118,6 +118,8 @@ size_t tables_bytes(int nx, int ny) {
 
 }  // namespace
 
+void cwo::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 // ------------------------------------------------------------------------------------------
 // plan
 // ------------------------------------------------------------------------------------------
