@@ -144,6 +144,11 @@ cwo_status cwo_propagate_adjoint_batch(cwo_plan* plan, const void* in, long long
  * accounting in benchmarks). */
 int cwo_launches_per_call(const cwo_plan* plan);
 
+/* Synchronise the device and report whether any earlier call on this plan had a bounded wait
+ * expire (CWO_ERR_TIMEOUT; the affected outputs were not written).  The waits guard asynchronous
+ * copies into shared memory; expiry means the device stalled for seconds.  Clears the record. */
+cwo_status cwo_plan_check(cwo_plan* plan);
+
 /* Instrumentation: when `events` is non-NULL it must point to 4 cudaEvent_t (passed as void*)
  * created by the caller on the plan's device; every later call records events[0] before the row
  * forward pass, events[1] after it, events[2] after the column pass and events[3] after the row

@@ -1,5 +1,6 @@
 // cwo_internal.h -- structures shared by the host plan code and the kernel launchers.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -47,12 +48,16 @@ struct HParams {
 void set_last_error(const char* msg);
 
 // The intermediate is column-major: [items][Px][Ny] complex64 (see cwo_rows.cu).
-cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, float2* w,
-                           long long w_item_stride, int ny, int items, const float4* tw,
-                           cudaStream_t st);
-cudaError_t launch_row_inv(int px, const float2* w, long long w_item_stride, float2* out,
-                           long long out_item_stride, int ny, int items, float scale,
-                           const float4* tw, cudaStream_t st);
+// The row passes reach the intermediate through rank-3 TMA tensor maps (Ny, Px, items) with
+// boxes of row_block_rows(px, inverse) rows x min(256, Px) columns (one map per pass);
+// item_off is added to the item index.
+int row_block_rows(int px, bool inverse);
+cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap,
+                           int item_off, int ny, int items, const float4* tw, cudaStream_t st);
+cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
+                           int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st);
+// Encode the tensor map of an intermediate [cap][px][ny] at base (host only; no allocation).
+cudaError_t make_intermediate_map(CUtensorMap* map, void* base, int ny, int px, int cap, int rows);
 cudaError_t launch_col(int py, const float2* win, long long win_item_stride, float2* wout,
                        long long wout_item_stride, int px, int items, const float4* tw,
                        const HParams& hp, cudaStream_t st);

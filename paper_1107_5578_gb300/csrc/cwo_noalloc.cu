@@ -43,6 +43,7 @@ static __device__ __align__(256) int g_kb_x[kMaxP];
 static __device__ __align__(256) int g_kb_y[kMaxP];
 static __device__ __align__(256) int2 g_pairs[kMaxP / 2 + 1];
 static __device__ __align__(256) float g_kf[1];
+static __device__ __align__(256) int g_status[1];
 
 struct Addrs {
     float2* scratch;
@@ -50,6 +51,7 @@ struct Addrs {
     int *kb_x, *kb_y;
     int2* pairs;
     float* kf;
+    int* status;
 };
 
 cwo_status fail(cwo_status st, const char* msg) {
@@ -85,7 +87,8 @@ cudaError_t resolve(int dev, Addrs* out) {
             (e = cudaGetSymbolAddress((void**)&a.tw_x, g_tw_x)) || (e = cudaGetSymbolAddress((void**)&a.tw_y, g_tw_y)) ||
             (e = cudaGetSymbolAddress((void**)&a.ax, g_ax)) || (e = cudaGetSymbolAddress((void**)&a.ay, g_ay)) ||
             (e = cudaGetSymbolAddress((void**)&a.kb_x, g_kb_x)) || (e = cudaGetSymbolAddress((void**)&a.kb_y, g_kb_y)) ||
-            (e = cudaGetSymbolAddress((void**)&a.pairs, g_pairs)) || (e = cudaGetSymbolAddress((void**)&a.kf, g_kf)))
+            (e = cudaGetSymbolAddress((void**)&a.pairs, g_pairs)) || (e = cudaGetSymbolAddress((void**)&a.kf, g_kf)) ||
+            (e = cudaGetSymbolAddress((void**)&a.status, g_status)))
             return e;
         g_addr[dev] = a;
         g_have[dev] = true;
@@ -231,9 +234,13 @@ extern "C" cwo_status cwo_propagate_asm_noalloc(int nx, int ny, double dx, doubl
     float2* fout = (float2*)out_c64;
     const long long field = (long long)nx * ny, wstride = (long long)ny * px;
     const float scale = (float)(1.0 / ((double)px * (double)py));
-    if ((e = cwo::launch_row_fwd(px, fin, field, a.scratch, wstride, ny, 1, a.tw_x, s)) ||
+    CUtensorMap wmap_f, wmap_i;   // host-side descriptions of g_scratch for the TMA copies (no allocation)
+    if (cwo::make_intermediate_map(&wmap_f, a.scratch, ny, px, 1, cwo::row_block_rows(px, false)) != cudaSuccess ||
+        cwo::make_intermediate_map(&wmap_i, a.scratch, ny, px, 1, cwo::row_block_rows(px, true)) != cudaSuccess)
+        return fail(CWO_ERR_CUDA, "tensor map of the fixed scratch");
+    if ((e = cwo::launch_row_fwd(px, fin, field, &wmap_f, 0, ny, 1, a.tw_x, s)) ||
         (e = cwo::launch_col(py, a.scratch, wstride, a.scratch, wstride, px, 1, a.tw_y, hp, s)) ||
-        (e = cwo::launch_row_inv(px, a.scratch, wstride, fout, field, ny, 1, scale, a.tw_x, s)))
+        (e = cwo::launch_row_inv(px, &wmap_i, 0, fout, field, ny, 1, scale, a.tw_x, a.status, s)))
         return fail(CWO_ERR_CUDA, cudaGetErrorString(e));
     return CWO_OK;
 }

@@ -150,6 +150,9 @@ struct cwo_plan {
     int scap = 0;
     // optional per-pass timing events (caller-owned)
     cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+    CUtensorMap wmap_f;        // TMA maps of the scratch intermediate [scap][px][ny] for the
+    CUtensorMap wmap_i;        // forward and inverse row passes (different box heights)
+    int* status = nullptr;     // device status word: bounded waits that expired (cwo_plan_check)
 };
 
 namespace {
@@ -164,6 +167,7 @@ void free_plan(cwo_plan* p) {
     if (p->zhost) cudaFreeHost(p->zhost);
     if (p->zev) cudaEventDestroy(p->zev);
     cudaFree(p->scratch);
+    cudaFree(p->status);
     delete p;
 }
 
@@ -204,6 +208,9 @@ cwo_status ensure_scratch(cwo_plan* p, int items) {
     p->scap = 0;
     cwo_status st = dev_alloc(&p->scratch, (size_t)items * p->ny * p->px, "scratch");
     if (st != CWO_OK) return st;
+    if ((e = cwo::make_intermediate_map(&p->wmap_f, p->scratch, p->ny, p->px, items, cwo::row_block_rows(p->px, false))) ||
+        (e = cwo::make_intermediate_map(&p->wmap_i, p->scratch, p->ny, p->px, items, cwo::row_block_rows(p->px, true))))
+        return cuda_fail(e, "tensor map of the intermediate");
     p->scap = items;
     return CWO_OK;
 }
@@ -352,7 +359,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         // the shared source: row pass once, then per-plane column and inverse row passes
         float2* w0 = p->scratch;
         float2* wz = p->scratch + wstride;
-        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, 0, w0, 0, p->ny, 1, p->tw_x, s)) || (e = mark(1)))
+        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, 0, &p->wmap_f, 0, p->ny, 1, p->tw_x, s)) || (e = mark(1)))
             return cuda_fail(e, "row forward launch");
         if (per_item_k) {
             for (int i = 0; i < batch; ++i) {
@@ -364,11 +371,11 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         } else if ((e = cwo::launch_col(p->py, w0, 0, wz, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2))) {
             return cuda_fail(e, "column launch");
         }
-        if ((e = cwo::launch_row_inv(p->px, wz, wstride, fout, field, p->ny, batch, scale, p->tw_x, s)) || (e = mark(3)))
+        if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 1, fout, field, p->ny, batch, scale, p->tw_x, p->status, s)) || (e = mark(3)))
             return cuda_fail(e, "row inverse launch");
     } else {
         const long long istr = in_stride ? in_stride : field;
-        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, istr, p->scratch, wstride, p->ny, batch, p->tw_x, s)) || (e = mark(1)))
+        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, istr, &p->wmap_f, 0, p->ny, batch, p->tw_x, s)) || (e = mark(1)))
             return cuda_fail(e, "row forward launch");
         if (per_item_k) {
             for (int i = 0; i < batch; ++i) {
@@ -381,7 +388,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         } else if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2))) {
             return cuda_fail(e, "column launch");
         }
-        if ((e = cwo::launch_row_inv(p->px, p->scratch, wstride, fout, field, p->ny, batch, scale, p->tw_x, s)) || (e = mark(3)))
+        if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 0, fout, field, p->ny, batch, scale, p->tw_x, p->status, s)) || (e = mark(3)))
             return cuda_fail(e, "row inverse launch");
     }
     return CWO_OK;
@@ -446,6 +453,8 @@ cwo_status cwo_plan_create(int nx, int ny, double dx, double dy, double lambda, 
         if ((st = dev_alloc(&p->hx, hx.size(), "x table")) || (st = upload(p->hx, hx, "x table upload")) ||
             (st = dev_alloc(&p->hy, hy.size(), "y table")) || (st = upload(p->hy, hy, "y table upload"))) { free_plan(p); return st; }
     }
+    if ((st = dev_alloc(&p->status, 1, "status word"))) { free_plan(p); return st; }
+    if ((e = cudaMemset(p->status, 0, sizeof(int))) != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaMemset"); }
     if ((st = ensure_scratch(p, 1))) { free_plan(p); return st; }
     *out = p;
     return CWO_OK;
@@ -486,6 +495,20 @@ cwo_status cwo_propagate_adjoint_batch(cwo_plan* plan, const void* in, long long
 }
 
 int cwo_launches_per_call(const cwo_plan* plan) { return plan ? 3 : 0; }
+
+cwo_status cwo_plan_check(cwo_plan* plan) {
+    if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
+    cwo_status st = check_plan_device(plan);
+    if (st) return st;
+    int word = 0;
+    cudaError_t e = cudaMemcpy(&word, plan->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
+    if (word) {
+        if ((e = cudaMemset(plan->status, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "clearing the status word");
+        return fail(CWO_ERR_TIMEOUT, "a bounded wait on an asynchronous copy expired; the affected output was not written");
+    }
+    return CWO_OK;
+}
 
 cwo_status cwo_plan_set_timing_events(cwo_plan* plan, void* const* events) {
     if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");

@@ -12,80 +12,86 @@
 // values of one frequency kx contiguously, so that the column pass streams whole columns.  Along
 // x the storage order is the register order of the last forward stage: register e of thread t
 // (DIF position 16 t + e) is storage column e * T + t.  A CTA handles R rows and transposes them
-// through a padded shared-memory tile, so that each group of R lanes writes (reads) R
-// consecutive values of one storage column: R * 8 contiguous bytes per lane group.
+// through a dense shared-memory tile [st][r]; the tile moves to and from the intermediate as TMA
+// tensor boxes of R rows x 256 columns (R * 8 contiguous bytes per column), so the transposed
+// global side costs the threads no load/store instructions.
 #include "cwo_fft.cuh"
 #include "cwo_internal.h"
+#include "cwo_tma.cuh"
 
 namespace cwo {
 
-// threads per row-pass CTA (compile-time tuning knob)
-#ifndef CWO_ROW_THREADS
-#define CWO_ROW_THREADS 1024
-#endif
-template <int P> constexpr int rows_per_block() {
-    constexpr int T = P / 16;
-    constexpr int r = CWO_ROW_THREADS / T;
-    return r < 1 ? 1 : (r > 8 ? 8 : r);
-}
+// Rows per CTA of each pass (measured on GB300).  The forward pass stores its tile, and stores of
+// less than a 32-byte sector per column are expensive, so it keeps >= 4 rows where a 4-row tile
+// fits (P <= 4096); the inverse pass loads, where 2-row tiles (16 bytes per column, the other half
+// of each sector served from L2 to the neighbouring CTA) allow more CTAs per SM.  A TMA box must
+// span at least 16 contiguous bytes, hence >= 2 rows.
+template <int P> constexpr int rows_fwd() { return P >= 8192 ? 2 : (P >= 4096 ? 4 : (P >= 256 ? 4 : 8)); }
+template <int P> constexpr int rows_inv() { return P >= 4096 ? 2 : (P >= 256 ? 4 : 8); }
 
 template <int P, int R>
-constexpr size_t row_smem_words() {
-    return PadLayout<P, R>::WORDS > TileLayout<P, R>::WORDS ? PadLayout<P, R>::WORDS : TileLayout<P, R>::WORDS;
+__host__ __device__ constexpr size_t row_smem_words() {
+    return PadLayout<P, R>::WORDS > (size_t)R * P ? PadLayout<P, R>::WORDS : (size_t)R * P;
 }
+
+// Lanes are row-fastest (thread = r + R t): the FFT exchanges then see R interleaved transforms,
+// for which the padded layout is conflict free, and the dense tile [st][r] used by the transposing
+// copies is addressed as e * (R T) + threadIdx.x, i.e. consecutive words across a warp.
 
 template <int P, int R>
 __global__ void __launch_bounds__(R * (P / 16))
-k_row_fwd(const float2* __restrict__ in, long long in_item_stride, float2* __restrict__ w,
-          long long w_item_stride, int ny, const float4* __restrict__ tw) {
+k_row_fwd(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap wmap,
+          int item_off, const float4* __restrict__ tw) {
     constexpr int T = P / 16, N = P / 2, NT = R * T;
-    using Tile = TileLayout<P, R>;
-    extern __shared__ float2 sm[];
-    const int t = threadIdx.x % T, r = threadIdx.x / T;
-    const long long y0 = (long long)blockIdx.x * R;
-    const long long item = blockIdx.y;
-    const float2* src = in + item * in_item_stride + (y0 + r) * N;
+    constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
+    extern __shared__ __align__(1024) float2 sm[];
+    const int r = threadIdx.x % R, t = threadIdx.x / R;
+    const int y0 = blockIdx.x * R;
+    const int item = blockIdx.y;
+    const float2* src = in + item * in_item_stride + (long long)(y0 + r) * N;
     float2 v[16];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = __ldg(src + t + e * T);   // DIF stage-0 positions t + e P/16
 #pragma unroll
     for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);   // zero padding, never loaded
     fwd_from<P, R, PadLayout<P, R>, 0, 8, 0>(v, sm, r, t, TwTable<P>{tw, t});
-    // transpose: register e of (r, t) is storage column st = e T + t of row y0 + r
+    // dense tile [st][r]: register e of (r, t) is storage column st = e T + t of row y0 + r
 #pragma unroll
-    for (int e = 0; e < 16; ++e) sm[Tile::addr(e * T + t, r)] = v[e];
+    for (int e = 0; e < 16; ++e) sm[e * NT + threadIdx.x] = v[e];
+    fence_proxy_async_smem();
     __syncthreads();
-    float2* dst = w + item * w_item_stride + y0;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const int i = threadIdx.x + k * NT;          // i = st * R + rr
-        dst[(long long)(i / R) * ny + (i % R)] = sm[i + (i >> 4)];
+    if (threadIdx.x == 0) {   // R rows x BOX columns per box: R * 8 contiguous bytes per column
+#pragma unroll 1
+        for (int b = 0; b < P / BOX; ++b) tma_store_3d(&wmap, sm + b * BOX * R, y0, b * BOX, item + item_off);
+        tma_store_commit_and_drain();
     }
 }
 
 template <int P, int R>
 __global__ void __launch_bounds__(R * (P / 16))
-k_row_inv(const float2* __restrict__ w, long long w_item_stride, float2* __restrict__ out,
-          long long out_item_stride, int ny, float scale, const float4* __restrict__ tw) {
+k_row_inv(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __restrict__ out,
+          long long out_item_stride, float scale, const float4* __restrict__ tw, int* status) {
     constexpr int T = P / 16, N = P / 2, NT = R * T;
-    using Tile = TileLayout<P, R>;
-    extern __shared__ float2 sm[];
-    const int t = threadIdx.x % T, r = threadIdx.x / T;
-    const long long y0 = (long long)blockIdx.x * R;
-    const long long item = blockIdx.y;
-    const float2* src = w + item * w_item_stride + y0;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const int i = threadIdx.x + k * NT;
-        sm[i + (i >> 4)] = src[(long long)(i / R) * ny + (i % R)];
-    }
+    constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
+    extern __shared__ __align__(1024) float2 sm[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + row_smem_words<P, R>());   // after the tile
+    const int r = threadIdx.x % R, t = threadIdx.x / R;
+    const int y0 = blockIdx.x * R;
+    const int item = blockIdx.y;
+    if (threadIdx.x == 0) mbar_init(mbar, 1);
     __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(mbar, (unsigned)(R * P * sizeof(float2)));
+#pragma unroll 1
+        for (int b = 0; b < P / BOX; ++b) tma_load_3d(sm + b * BOX * R, &wmap, mbar, y0, b * BOX, item + item_off);
+    }
+    const bool ok = mbar_wait_bounded(mbar, 0, status);
     float2 v[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = sm[Tile::addr(e * T + t, r)];
-    __syncthreads();
+    for (int e = 0; e < 16; ++e) v[e] = sm[e * NT + threadIdx.x];
+    if (__syncthreads_or(!ok)) return;             // a copy did not land: the status word says so
     inv_from<P, R, PadLayout<P, R>, Geo<P>::NST - 1, 0, 0>(v, sm, r, t, TwTable<P>{tw, t});
-    float2* dst = out + item * out_item_stride + (y0 + r) * N;
+    float2* dst = out + item * out_item_stride + (long long)(y0 + r) * N;
 #pragma unroll
     for (int e = 0; e < 8; ++e) dst[t + e * T] = cscale(v[e], scale);   // crop: first Nx outputs
 }
@@ -97,53 +103,91 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
 }
 
 template <int P>
-static cudaError_t row_fwd_impl(const float2* in, long long in_item_stride, float2* w,
-                                long long w_item_stride, int ny, int items, const float4* tw,
-                                cudaStream_t st) {
-    constexpr int R = rows_per_block<P>();
+static cudaError_t row_fwd_impl(const float2* in, long long in_item_stride, const CUtensorMap* wmap,
+                                int item_off, int ny, int items, const float4* tw, cudaStream_t st) {
+    constexpr int R = rows_fwd<P>();
     constexpr int T = P / 16;
     const size_t smem = row_smem_words<P, R>() * sizeof(float2);
     cudaError_t e = ensure_smem(k_row_fwd<P, R>, smem);
     if (e != cudaSuccess) return e;
     if (ny % R) return cudaErrorInvalidValue;
     dim3 grid(ny / R, items);
-    k_row_fwd<P, R><<<grid, R * T, smem, st>>>(in, in_item_stride, w, w_item_stride, ny, tw);
+    k_row_fwd<P, R><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, tw);
     return cudaGetLastError();
 }
 
 template <int P>
-static cudaError_t row_inv_impl(const float2* w, long long w_item_stride, float2* out,
-                                long long out_item_stride, int ny, int items, float scale,
-                                const float4* tw, cudaStream_t st) {
-    constexpr int R = rows_per_block<P>();
+static cudaError_t row_inv_impl(const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
+                                int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st) {
+    constexpr int R = rows_inv<P>();
     constexpr int T = P / 16;
-    const size_t smem = row_smem_words<P, R>() * sizeof(float2);
+    const size_t smem = row_smem_words<P, R>() * sizeof(float2) + sizeof(uint64_t);   // tile + mbarrier
     cudaError_t e = ensure_smem(k_row_inv<P, R>, smem);
     if (e != cudaSuccess) return e;
     if (ny % R) return cudaErrorInvalidValue;
     dim3 grid(ny / R, items);
-    k_row_inv<P, R><<<grid, R * T, smem, st>>>(w, w_item_stride, out, out_item_stride, ny, scale, tw);
+    k_row_inv<P, R><<<grid, R * T, smem, st>>>(*wmap, item_off, out, out_item_stride, scale, tw, status);
     return cudaGetLastError();
 }
 
 #define CWO_P_CASES(X) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
 
-cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, float2* w,
-                           long long w_item_stride, int ny, int items, const float4* tw,
-                           cudaStream_t st) {
+typedef CUresult (*PFN_tensorMapEncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                              CUtensorMapFloatOOBfill);
+
+static PFN_tensorMapEncodeTiled encode_fn() {
+    static PFN_tensorMapEncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {   // resolved through the runtime: no link-time dependency on libcuda
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_tensorMapEncodeTiled)p;
+        tried = true;
+    }
+    return fn;
+}
+
+cudaError_t make_intermediate_map(CUtensorMap* map, void* base, int ny, int px, int cap, int rows) {
+    PFN_tensorMapEncodeTiled fn = encode_fn();
+    const int R = rows;
+    if (!fn || R < 2 || cap < 1 || ny % R) return cudaErrorInvalidValue;
+    const cuuint64_t dims[3] = {(cuuint64_t)ny, (cuuint64_t)px, (cuuint64_t)cap};
+    const cuuint64_t strides[2] = {(cuuint64_t)ny * sizeof(float2), (cuuint64_t)ny * px * sizeof(float2)};
+    const cuuint32_t box[3] = {(cuuint32_t)R, (cuuint32_t)(px < kTmaBoxCols ? px : kTmaBoxCols), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int row_block_rows(int px, bool inverse) {
     switch (px) {
-#define CASE(P) case P: return row_fwd_impl<P>(in, in_item_stride, w, w_item_stride, ny, items, tw, st);
+#define CASE(P) case P: return inverse ? rows_inv<P>() : rows_fwd<P>();
+        CWO_P_CASES(CASE)
+#undef CASE
+        default: return 0;
+    }
+}
+
+cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap,
+                           int item_off, int ny, int items, const float4* tw, cudaStream_t st) {
+    switch (px) {
+#define CASE(P) case P: return row_fwd_impl<P>(in, in_item_stride, wmap, item_off, ny, items, tw, st);
         CWO_P_CASES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_row_inv(int px, const float2* w, long long w_item_stride, float2* out,
-                           long long out_item_stride, int ny, int items, float scale,
-                           const float4* tw, cudaStream_t st) {
+cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
+                           int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st) {
     switch (px) {
-#define CASE(P) case P: return row_inv_impl<P>(w, w_item_stride, out, out_item_stride, ny, items, scale, tw, st);
+#define CASE(P) case P: return row_inv_impl<P>(wmap, item_off, out, out_item_stride, ny, items, scale, tw, status, st);
         CWO_P_CASES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;

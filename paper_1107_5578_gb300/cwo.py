@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
                 "cwo_propagate_adjoint": ([vp, vp, vp, vp], i),
                 "cwo_propagate_adjoint_batch": ([vp, vp, ll, vp, i, dpp, vp], i),
                 "cwo_launches_per_call": ([vp], i),
+                "cwo_plan_check": ([vp], i),
                 "cwo_plan_set_timing_events": ([vp, ctypes.POINTER(ctypes.c_void_p)], i),
                 "cwo_last_error": ([], ctypes.c_char_p),
                 "cwo_version": ([], i),
@@ -148,6 +149,11 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def check(self) -> None:
+        """Synchronise and raise CwoError(CWO_ERR_TIMEOUT) if a bounded wait of an earlier call
+        on this plan expired."""
+        check(lib().cwo_plan_check(self.handle), "cwo_plan_check")
 
     def reserve(self, batch: int) -> None:
         check(lib().cwo_plan_reserve(self.handle, int(batch)), "cwo_plan_reserve")

@@ -194,3 +194,13 @@ def test_fresnel_stack_2048_sampled_planes(cwo):
         want = oracle.propagate(u, 8e-6, 8e-6, 532e-9, float(zs[j]), oracle.FRESNEL_CONV)
         assert rel(to_host(y[j]), want) <= TOL
     plan.close()
+
+
+def test_status_word_stays_clean(cwo):
+    # the bounded waits of the row passes never expire in normal operation
+    u = synth.random_field(256, seed=12)
+    plan = cwo.Plan(256, None, 10e-6, None, 633e-9, 0.05, 0)
+    for _ in range(3):
+        plan.propagate(to_dev(u))
+    plan.check()
+    plan.close()
