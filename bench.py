@@ -155,6 +155,37 @@ def cpu_baseline_sample():
             "sample": f"{reps} propagation(s) of one 2048^2 ASM field (FP64, OpenMP over rows/columns)"}
 
 
+def stack_measurement(dev, hbm_peak):
+    """The 2048^2 Fresnel z-stack: a seeded Bernoulli(0.5) mask times a Gaussian envelope
+    (sigma = 400 px), 532 nm, 8 um, 16 planes z = linspace(0.1, 0.4, 16), all planes in one
+    batched call.  Algorithmic bytes: 680 N^2 (source read once, 16 planes written, the shared
+    spectrum read once and each plane's intermediate written and read once)."""
+    import torch
+    from paper_1107_5578_gb300 import cwo, synth
+    n, planes = 2048, 16
+    zs = [float(v) for v in np.linspace(0.1, 0.4, planes)]
+    x = torch.from_numpy(synth.masked_gaussian(n, seed=2).astype(np.complex64)).to(dev)
+    plan = cwo.Plan(n, n, 8e-6, 8e-6, 532e-9, zs[0], cwo.FRESNEL_CONV)
+    plan.reserve(planes)
+    y = torch.empty((planes, n, n), dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        plan.propagate_stack(x, zs, out=y)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    a.record()
+    for _ in range(reps):
+        plan.propagate_stack(x, zs, out=y)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    gbs = 680 * n * n / (ms / 1e3) / 1e9
+    plan.close()
+    return {"workload": "fresnel_2048_pad4096_stack16", "ms_per_stack": round(ms, 4),
+            "planes_per_s": round(planes / (ms / 1e3), 1), "hbm_gbs_algorithmic": round(gbs, 1),
+            "frac_of_measured_hbm": round(gbs / hbm_peak, 4), "launches_per_stack": 3}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -260,6 +291,7 @@ def main():
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e_value = B * e_steps * world / (float(te.item()) / 1e3)
 
+    stack = stack_measurement(dev, peaks()[0])
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
@@ -285,6 +317,7 @@ def main():
         "e2e": {"value": round(e_value, 2), "unit": UNIT,
                 "h2d_bytes_per_step": B * N * N * 8, "d2h_bytes_per_step": B * N * N * 8},
         "gpu_launches": plan.launches_per_call * args.steps,
+        "fresnel_stack": stack,
         "wall_s": round(wall1 - wall0, 3),
         "cpu_baseline": cpu,
     }

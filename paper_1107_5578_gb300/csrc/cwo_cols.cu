@@ -148,6 +148,40 @@ k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __rest
     }
 }
 
+// Shared-source z-stack: the forward column transform of the source is computed once and kept
+// in registers; for each plane the kernel multiplies a copy by that plane's transfer function,
+// transforms it back and writes the plane (Section "Three-dimensional diffraction calculations":
+// a stack of 2-D diffractions of one source).
+template <int P, int C>
+__global__ void __launch_bounds__(C * (P / 16), col_min_blocks<P>())
+k_col_stack(const float2* __restrict__ win, float2* __restrict__ wout, long long wout_item_stride, int nplanes,
+            const float4* __restrict__ tw, const HParams hp) {
+    constexpr int T = P / 16, NY = P / 2;
+    using Lay = PadLayout<P, C>;
+    extern __shared__ float2 sm[];
+    const int t = threadIdx.x % T, c = threadIdx.x / T;
+    const int col = blockIdx.x * C + c;
+    const float2* src = win + (long long)col * NY;
+    float2 spec[16];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) spec[e] = src[t + e * T];
+#pragma unroll
+    for (int e = 8; e < 16; ++e) spec[e] = make_float2(0.f, 0.f);
+    const TwTable<P> twt{tw, t};
+    fwd_from<P, C, Lay, 0, 8, 0>(spec, sm, c, t, twt);
+#pragma unroll 1
+    for (int z = 0; z < nplanes; ++z) {
+        float2 v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = spec[e];
+        apply_h<P, 1>(v, v, col, t, z, hp);
+        inv_from<P, C, Lay, Geo<P>::NST - 1, 0, 0>(v, sm, c, t, twt);
+        float2* dst = wout + z * wout_item_stride + (long long)col * NY;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[t + e * T] = v[e];
+    }
+}
+
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
@@ -175,6 +209,29 @@ static cudaError_t col_impl(const float2* win, long long win_item_stride, float2
         k_col<P, C><<<dim3(px / C, items), C * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
     }
     return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t col_stack_impl(const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
+                                  const float4* tw, const HParams& hp, cudaStream_t st) {
+    constexpr int C = cols_per_block<P>();
+    constexpr int T = P / 16;
+    if (px % C != 0) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
+    cudaError_t e;
+    if ((e = set_smem(k_col_stack<P, C>, smem))) return e;
+    k_col_stack<P, C><<<px / C, C * T, smem, st>>>(win, wout, wout_item_stride, planes, tw, hp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_stack(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
+                             const float4* tw, const HParams& hp, cudaStream_t st) {
+    switch (py) {
+#define CASE(P) case P: return col_stack_impl<P>(win, wout, wout_item_stride, px, planes, tw, hp, st);
+        CASE(32) CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024) CASE(2048) CASE(4096) CASE(8192)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_col(int py, const float2* win, long long win_item_stride, float2* wout,

@@ -56,6 +56,9 @@ cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, c
                            int item_off, int ny, int items, const float4* tw, cudaStream_t st);
 cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
                            int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st);
+// column pass of a shared-source z-stack: one forward transform per column, `planes` outputs
+cudaError_t launch_col_stack(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
+                             const float4* tw, const HParams& hp, cudaStream_t st);
 // Encode the tensor map of an intermediate [cap][px][ny] at base (host only; no allocation).
 cudaError_t make_intermediate_map(CUtensorMap* map, void* base, int ny, int px, int cap, int rows);
 cudaError_t launch_col(int py, const float2* win, long long win_item_stride, float2* wout,

@@ -145,6 +145,7 @@ struct cwo_plan {
     float* zkf = nullptr;
     void* zhost = nullptr; size_t zhost_bytes = 0;   // pinned staging
     cudaEvent_t zev = nullptr; bool zev_pending = false;
+    std::vector<double> zs_cached;   // distances whose tables the per-item buffers hold
     // scratch intermediate [cap][ny][px]
     float2* scratch = nullptr;
     int scap = 0;
@@ -217,6 +218,7 @@ cwo_status ensure_scratch(cwo_plan* p, int items) {
 
 cwo_status ensure_ztables(cwo_plan* p, int items) {
     if (items <= p->zcap) return CWO_OK;
+    p->zs_cached.clear();
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize before growing tables");
     cudaFree(p->zax); cudaFree(p->zay); cudaFree(p->zhx); cudaFree(p->zhy); cudaFree(p->zkf);
@@ -307,7 +309,19 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     // FP64 per element with per-item distances: one launch set per item, each with its own K
     const bool per_item_k = zs && hp.mode == cwo::HMODE_ASM_FP64;
 
-    if (zs && !per_item_k) {
+    // per-item tables of the same distances as the previous call are reused ("once-calculation")
+    const bool ztables_hit = zs && !per_item_k && (int)p->zs_cached.size() == batch &&
+                             std::equal(p->zs_cached.begin(), p->zs_cached.end(), zs);
+    if (zs && !per_item_k && ztables_hit) {
+        if (p->type == CWO_ANGULAR) {
+            hp.ax = p->zax; hp.ay = p->zay; hp.kf = p->zkf;
+            hp.x_item_stride = p->px; hp.y_item_stride = p->py; hp.kf_item_stride = 1;
+        } else {
+            hp.hx = p->zhx; hp.hy = p->zhy;
+            hp.x_item_stride = p->px; hp.y_item_stride = p->py;
+        }
+    } else if (zs && !per_item_k) {
+        p->zs_cached.clear();
         if ((st = ensure_ztables(p, batch))) return st;
         if (p->zev_pending) {   // the staging buffer may still feed the previous upload
             cudaError_t e = cudaEventSynchronize(p->zev);
@@ -343,6 +357,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         cudaError_t e = cudaEventRecord(p->zev, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         p->zev_pending = true;
+        p->zs_cached.assign(zs, zs + batch);
     } else {
         hp.ax = p->ax; hp.ay = p->ay; hp.kf = p->kf; hp.hx = p->hx; hp.hy = p->hy;
         hp.x_item_stride = 0; hp.y_item_stride = 0; hp.kf_item_stride = 0;
@@ -368,7 +383,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
                     return cuda_fail(e, "column launch");
             }
             if ((e = mark(2))) return cuda_fail(e, "event");
-        } else if ((e = cwo::launch_col(p->py, w0, 0, wz, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2))) {
+        } else if ((e = cwo::launch_col_stack(p->py, w0, wz, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2))) {
             return cuda_fail(e, "column launch");
         }
         if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 1, fout, field, p->ny, batch, scale, p->tw_x, p->status, s)) || (e = mark(3)))
