@@ -129,6 +129,27 @@ cwo_status cwo_propagate(cwo_plan* plan, const void* in_c64, void* out_c64, void
 cwo_status cwo_propagate_batch(cwo_plan* plan, const void* in, long long in_batch_stride,
                                void* out, int batch, const double* z_or_null, void* cuda_stream);
 
+/* One item of a mixed batch: its own diffraction type and parameters (same Nx x Ny as the plan). */
+typedef struct {
+    double z;         /* distance, metres (non-zero for CWO_FRESNEL_CONV)           */
+    double lambda;    /* wavelength, metres (> 0)                                   */
+    double dx, dy;    /* sampling pitches, metres (> 0)                             */
+    int type;         /* CWO_ANGULAR or CWO_FRESNEL_CONV                            */
+    unsigned flags;   /* 0, or CWO_FLAG_LITERAL_SCALE for a Fresnel item            */
+} cwo_item;
+
+/*
+ * Mixed batch: `batch` fields of the plan's Nx x Ny, item i propagated with items[i] (type,
+ * distance, wavelength, pitches), in one set of launches -- the batching step of a serving loop
+ * that groups same-size requests.  The plan supplies the shape, the scratch and the FFT tables;
+ * its own wavelength, pitches, distance and type are not used.  items is a HOST array; the
+ * per-item transfer-function tables are computed in FP64 on the host (in parallel threads) and
+ * uploaded stream-ordered.  in_batch_stride as in cwo_propagate_batch but must be > 0.
+ * Results are bit-identical to running each item alone (no arithmetic depends on the batch).
+ */
+cwo_status cwo_propagate_items(cwo_plan* plan, const void* in, long long in_batch_stride, void* out,
+                               int batch, const cwo_item* items, void* cuda_stream);
+
 /* Adjoint propagation: the same passes with conj(H) (and conj(C)), i.e. the conjugate
  * transpose of the linear map cwo_propagate applies; for CWO_ANGULAR without evanescent bins
  * it equals back-propagation by -z (Section "Field type", back propagation of List

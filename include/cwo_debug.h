@@ -2,8 +2,8 @@
  * cwo_debug.h -- host-only diagnostic entry points of libcwo_gb300.so.
  *
  * They expose the FP64 host computations the plans are built from, so that tests can check them
- * on a machine without a GPU.  None of them touches a device.  They return CWO_ERR_INVALID_ARG on
- * bad arguments (message in cwo_last_error()).
+ * on a machine without a GPU.  None of them touches a device, except cwo_debug_bounded_wait (the
+ * last one).  They return CWO_ERR_INVALID_ARG on bad arguments (message in cwo_last_error()).
  */
 #ifndef CWO_DEBUG_H
 #define CWO_DEBUG_H
@@ -48,6 +48,14 @@ cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, double lambda
  * order.  inverse = 1: adjoint of p axis-index-order values, returning the first p/2 natural-order
  * outputs (unscaled). */
 cwo_status cwo_debug_line_fft(int p, int inverse, const float* in_ri, float* out_ri);
+
+/* Failure path of the bounded mbarrier wait that guards every TMA load (device, current CUDA
+ * device, synchronous).  One thread initialises an mbarrier for one arrival; with complete = 0 it
+ * never arrives, so the wait can only end by its iteration limit: the kernel must then set the
+ * timeout bit (1) in a device status word and return.  With complete = 1 it arrives first and
+ * the status word stays 0.  spin_limit: polls before giving up, in [1, 2^20].  *status_out
+ * receives the status word.  Returns CWO_ERR_CUDA if the launch or a copy fails. */
+cwo_status cwo_debug_bounded_wait(unsigned spin_limit, int complete, int* status_out);
 
 #ifdef __cplusplus
 }

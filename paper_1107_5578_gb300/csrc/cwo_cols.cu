@@ -40,7 +40,7 @@ __device__ __forceinline__ float2 asm_h_fp32(int kbx, int kby, const HParams& hp
 }
 
 // multiply the registers of NV transforms of the same storage column pair (same |kx|) by H
-template <int P, int NV>
+template <int P, int NV, bool MIXED = false>
 __device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int col, int t, long long item,
                                         const HParams& hp) {
     constexpr int T = P / 16;
@@ -48,16 +48,37 @@ __device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int co
         a[e] = hp.conj ? cmulc(a[e], h) : cmul(a[e], h);
         if (NV == 2) b[e] = hp.conj ? cmulc(b[e], h) : cmul(b[e], h);
     };
-    if (hp.mode == HMODE_FRESNEL) {
-        const float2 hxc = __ldg(hp.hx + item * hp.x_item_stride + col);
-        const float2* hy = hp.hy + item * hp.y_item_stride + t;
+    int mode = hp.mode;
+    float K = 0.f;
+    double Kd = hp.K, sx = hp.sx, sy = hp.sy;
+    if (MIXED) {      // mixed batch: this item's own mode and scalars (uniform across the block)
+        const ItemParams ip = hp.items[item];
+        mode = ip.mode;
+        K = ip.kf;
+        Kd = ip.K; sx = ip.sx; sy = ip.sy;
+    } else if (mode == HMODE_ASM_POLY || mode == HMODE_ASM_EXACT) {
+        K = __ldg(hp.kf + item * hp.kf_item_stride);
+    }
+    if (mode == HMODE_FRESNEL) {
+        if (MIXED) {
+            const float4 X = __ldg(hp.ax + item * hp.x_item_stride + col);
+            const float2 hxc = make_float2(X.x, X.y);
+            const float4* hy = hp.ay + item * hp.y_item_stride + t;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) mul(e, cmul(hxc, __ldg(hy + e * T)));
-    } else if (hp.mode == HMODE_ASM_POLY || hp.mode == HMODE_ASM_EXACT) {
+            for (int e = 0; e < 16; ++e) {
+                const float4 Y = __ldg(hy + e * T);
+                mul(e, cmul(hxc, make_float2(Y.x, Y.y)));
+            }
+        } else {
+            const float2 hxc = __ldg(hp.hx + item * hp.x_item_stride + col);
+            const float2* hy = hp.hy + item * hp.y_item_stride + t;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) mul(e, cmul(hxc, __ldg(hy + e * T)));
+        }
+    } else if (mode == HMODE_ASM_POLY || mode == HMODE_ASM_EXACT) {
         const float4 X = __ldg(hp.ax + item * hp.x_item_stride + col);
         const float4* ay = hp.ay + item * hp.y_item_stride + t;
-        const float K = __ldg(hp.kf + item * hp.kf_item_stride);
-        if (hp.mode == HMODE_ASM_POLY) {
+        if (mode == HMODE_ASM_POLY) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) mul(e, asm_h_reduced<true>(X, __ldg(ay + e * T), K));
         } else {
@@ -69,7 +90,7 @@ __device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int co
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
             const int kby = __ldg(hp.kby + e * T + t);
-            mul(e, hp.mode == HMODE_ASM_FP32 ? asm_h_fp32(kbx, kby, hp) : asm_h_fp64(kbx, kby, hp.K, hp.sx, hp.sy));
+            mul(e, mode == HMODE_ASM_FP32 ? asm_h_fp32(kbx, kby, hp) : asm_h_fp64(kbx, kby, Kd, sx, sy));
         }
     }
 }
@@ -86,7 +107,7 @@ template <int P> constexpr int col_min_blocks() { return (P / 16) * cols_per_blo
 template <int P> constexpr bool col_paired() { return P <= 4096; }
 
 // single column per transform (used where the paired kernel would not fit in registers)
-template <int P, int C>
+template <int P, int C, bool MIXED>
 __global__ void __launch_bounds__(C * (P / 16), col_min_blocks<P>())
 k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
       long long wout_item_stride, const float4* __restrict__ tw, const HParams hp) {
@@ -104,7 +125,7 @@ k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restr
     for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);   // zero padding rows
     const TwTable<P> twt{tw, t};
     fwd_from<P, C, Lay, 0, 8, 0>(v, sm, c, t, twt);
-    apply_h<P, 1>(v, v, col, t, item, hp);
+    apply_h<P, 1, MIXED>(v, v, col, t, item, hp);
     inv_from<P, C, Lay, Geo<P>::NST - 1, 0, 0>(v, sm, c, t, twt);
     float2* dst = wout + item * wout_item_stride + (long long)col * NY;
 #pragma unroll
@@ -114,7 +135,7 @@ k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restr
 // Mirror-pair column kernel: a thread transforms the two storage columns of frequencies +kx and
 // -kx.  H depends on kx only through kx^2 (both methods), so the transfer function is evaluated
 // once for both, and the twiddles of each stage are loaded once for both.
-template <int P, int CP>
+template <int P, int CP, bool MIXED>
 __global__ void __launch_bounds__(CP * (P / 16), 2)
 k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
        long long wout_item_stride, const float4* __restrict__ tw, const HParams hp) {
@@ -134,7 +155,7 @@ k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __rest
 #pragma unroll
     for (int e = 8; e < 16; ++e) { a[e] = make_float2(0.f, 0.f); b[e] = make_float2(0.f, 0.f); }
     fwd2_from<P, 2 * CP, Lay, 0, 8, 0>(a, b, sm, 2 * cp, t, tw);
-    apply_h<P, 2>(a, b, pr.x, t, item, hp);
+    apply_h<P, 2, MIXED>(a, b, pr.x, t, item, hp);
     inv2_from<P, 2 * CP, Lay, Geo<P>::NST - 1, 0, 0>(a, b, sm, 2 * cp, t, tw);
     if (live) {
         float2* da = wout + item * wout_item_stride + (long long)pr.x * NY;
@@ -188,27 +209,35 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int P>
-static cudaError_t col_impl(const float2* win, long long win_item_stride, float2* wout,
-                            long long wout_item_stride, int px, int items, const float4* tw,
-                            const HParams& hp, cudaStream_t st) {
+template <int P, bool MIXED>
+static cudaError_t col_impl_t(const float2* win, long long win_item_stride, float2* wout,
+                              long long wout_item_stride, int px, int items, const float4* tw,
+                              const HParams& hp, cudaStream_t st) {
     constexpr int T = P / 16;
     cudaError_t e;
     if constexpr (col_paired<P>()) {
         constexpr int CP = cols_per_block<P>();
         const size_t smem = (size_t)PadLayout<P, 2 * CP>::WORDS * sizeof(float2);
-        if ((e = set_smem(k_colp<P, CP>, smem))) return e;
+        if ((e = set_smem(k_colp<P, CP, MIXED>, smem))) return e;
         if (hp.npairs != px / 2 + 1 || !hp.pairs) return cudaErrorInvalidValue;
         const unsigned blocks = (unsigned)((hp.npairs + CP - 1) / CP);
-        k_colp<P, CP><<<dim3(blocks, items), CP * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
+        k_colp<P, CP, MIXED><<<dim3(blocks, items), CP * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
     } else {
         constexpr int C = cols_per_block<P>();
         if (px % C != 0) return cudaErrorInvalidValue;
         const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
-        if ((e = set_smem(k_col<P, C>, smem))) return e;
-        k_col<P, C><<<dim3(px / C, items), C * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
+        if ((e = set_smem(k_col<P, C, MIXED>, smem))) return e;
+        k_col<P, C, MIXED><<<dim3(px / C, items), C * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
     }
     return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t col_impl(const float2* win, long long win_item_stride, float2* wout,
+                            long long wout_item_stride, int px, int items, const float4* tw,
+                            const HParams& hp, cudaStream_t st) {
+    return hp.items ? col_impl_t<P, true>(win, win_item_stride, wout, wout_item_stride, px, items, tw, hp, st)
+                    : col_impl_t<P, false>(win, win_item_stride, wout, wout_item_stride, px, items, tw, hp, st);
 }
 
 template <int P>

@@ -15,6 +15,15 @@ enum HMode : int {
     HMODE_FRESNEL = 4,       // Fresnel, separable table product
 };
 
+// Per-item parameters of a mixed batch (cwo_propagate_items): the item's transfer-function mode
+// and the scalars its per-element evaluation needs.  Its tables are float4 rows of the per-item
+// x/y tables (Fresnel items use .x, .y).
+struct ItemParams {
+    int mode;                 // HMode of this item
+    float kf;                 // K = z / lambda (series / closed-form tail)
+    double K, sx, sy;         // FP64 per-element arm
+};
+
 // Transfer-function description for the column pass.  Per-axis tables are indexed by the axis
 // index idx = e * T + t (register e of thread t in the last forward stage, i.e. DIF position
 // 16 t + e); along x the same index is the storage column of the intermediate.
@@ -41,6 +50,9 @@ struct HParams {
     // storage-column pairs (st(+kx), st(-kx)) for kx = 0 .. Px/2 (paired column kernel)
     const int2* pairs;
     int npairs;               // Px/2 + 1
+    // mixed batch: per-item modes and scalars (nullptr: the launch-wide fields above apply);
+    // the tables are then ax / ay (float4) with x_item_stride / y_item_stride for every mode
+    const ItemParams* items;
 };
 
 // launchers (return cudaGetLastError() after the launch)

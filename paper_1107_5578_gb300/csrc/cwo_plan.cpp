@@ -13,6 +13,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/cwo.h"
@@ -146,6 +147,11 @@ struct cwo_plan {
     void* zhost = nullptr; size_t zhost_bytes = 0;   // pinned staging
     cudaEvent_t zev = nullptr; bool zev_pending = false;
     std::vector<double> zs_cached;   // distances whose tables the per-item buffers hold
+    // mixed-batch (cwo_propagate_items) per-item tables and parameters
+    int icap = 0;
+    float4* ix = nullptr; float4* iy = nullptr; cwo::ItemParams* iprm = nullptr;
+    void* ihost = nullptr; size_t ihost_bytes = 0;
+    cudaEvent_t iev = nullptr; bool iev_pending = false;
     // scratch intermediate [cap][ny][px]
     float2* scratch = nullptr;
     int scap = 0;
@@ -169,6 +175,9 @@ void free_plan(cwo_plan* p) {
     if (p->zev) cudaEventDestroy(p->zev);
     cudaFree(p->scratch);
     cudaFree(p->status);
+    cudaFree(p->ix); cudaFree(p->iy); cudaFree(p->iprm);
+    if (p->ihost) cudaFreeHost(p->ihost);
+    if (p->iev) cudaEventDestroy(p->iev);
     delete p;
 }
 
@@ -409,6 +418,125 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     return CWO_OK;
 }
 
+cwo_status ensure_itables(cwo_plan* p, int items) {
+    if (items <= p->icap) return CWO_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize before growing item tables");
+    cudaFree(p->ix); cudaFree(p->iy); cudaFree(p->iprm);
+    p->ix = p->iy = nullptr; p->iprm = nullptr;
+    if (p->ihost) { cudaFreeHost(p->ihost); p->ihost = nullptr; }
+    p->icap = 0;
+    cwo_status st;
+    const size_t nx4 = (size_t)items * p->px, ny4 = (size_t)items * p->py;
+    if ((st = dev_alloc(&p->ix, nx4, "item x tables")) || (st = dev_alloc(&p->iy, ny4, "item y tables")) ||
+        (st = dev_alloc(&p->iprm, (size_t)items, "item parameters")))
+        return st;
+    p->ihost_bytes = (nx4 + ny4) * sizeof(float4) + (size_t)items * sizeof(cwo::ItemParams);
+    e = cudaMallocHost(&p->ihost, p->ihost_bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); p->ihost = nullptr; return fail(CWO_ERR_OOM, "pinned staging of %zu bytes failed", p->ihost_bytes); }
+    if (!p->iev) {
+        e = cudaEventCreateWithFlags(&p->iev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
+    p->icap = items;
+    return CWO_OK;
+}
+
+// the tables and scalars of one item of a mixed batch
+void item_tables(const cwo_plan* p, const cwo_item& it, float4* xt, float4* yt, cwo::ItemParams* prm) {
+    const AxisGeo gx(p->px), gy(p->py);
+    if (it.type == CWO_ANGULAR) {
+        asm_axis_table(gx, it.dx, it.lambda, it.z, true, xt);
+        asm_axis_table(gy, it.dy, it.lambda, it.z, false, yt);
+        const int tm = asm_tail_mode(p->px, p->py, it.dx, it.dy, it.lambda, it.z);
+        prm->mode = tm == 0 ? cwo::HMODE_ASM_POLY : tm == 1 ? cwo::HMODE_ASM_EXACT : cwo::HMODE_ASM_FP64;
+    } else {
+        std::vector<float2> hx(p->px), hy(p->py);
+        make_h_tables(p->px, p->py, it.dx, it.dy, it.lambda, it.z, true, (it.flags & CWO_FLAG_LITERAL_SCALE) != 0,
+                      nullptr, nullptr, hx.data(), hy.data(), nullptr);
+        for (int i = 0; i < p->px; ++i) xt[i] = make_float4(hx[i].x, hx[i].y, 0.f, 0.f);
+        for (int i = 0; i < p->py; ++i) yt[i] = make_float4(hy[i].x, hy[i].y, 0.f, 0.f);
+        prm->mode = cwo::HMODE_FRESNEL;
+    }
+    prm->kf = (float)(it.z / it.lambda);
+    prm->K = it.z / it.lambda;
+    prm->sx = it.lambda * it.lambda / ((double)p->px * it.dx * (double)p->px * it.dx);
+    prm->sy = it.lambda * it.lambda / ((double)p->py * it.dy * (double)p->py * it.dy);
+}
+
+cwo_status run_items(cwo_plan* p, const void* in, long long in_stride, void* out, int batch, const cwo_item* items,
+                     void* stream) {
+    if (!p) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
+    if (!items) return fail(CWO_ERR_INVALID_ARG, "items is NULL");
+    if (batch < 1 || batch > 65535) return fail(CWO_ERR_INVALID_ARG, "batch must be in [1, 65535] (got %d)", batch);
+    const long long field = (long long)p->nx * p->ny;
+    if (in_stride < field) return fail(CWO_ERR_INVALID_ARG, "input batch stride %lld smaller than one field (%lld)", in_stride, field);
+    for (int i = 0; i < batch; ++i) {
+        const cwo_item& it = items[i];
+        cwo_status st = check_params(p->nx, p->ny, it.dx, it.dy, it.lambda, it.z, it.type, it.flags);
+        if (st) return fail(st, "item %d: %s", i, g_err.c_str());
+        if (it.flags & (CWO_FLAG_PHASE_FP32 | CWO_FLAG_PHASE_FP64))
+            return fail(CWO_ERR_UNSUPPORTED, "item %d: phase-precision study flags are not provided in mixed batches", i);
+    }
+    cwo_status st = check_plan_device(p);
+    if (st) return st;
+    const size_t fb = (size_t)field * sizeof(float2);
+    if ((st = check_device_range(in, (size_t)(batch - 1) * in_stride * sizeof(float2) + fb, p->device, "input"))) return st;
+    if ((st = check_device_range(out, (size_t)batch * fb, p->device, "output"))) return st;
+    if ((st = ensure_scratch(p, batch)) || (st = ensure_itables(p, batch))) return st;
+    if (p->iev_pending) {
+        cudaError_t e = cudaEventSynchronize(p->iev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        p->iev_pending = false;
+    }
+    float4* hx = (float4*)p->ihost;
+    float4* hy = hx + (size_t)batch * p->px;
+    cwo::ItemParams* hp_items = (cwo::ItemParams*)(hy + (size_t)batch * p->py);
+    // per-item FP64 tables, items spread over host threads when there is enough work
+    const size_t work = (size_t)batch * (p->px + p->py);
+    const int nthreads = (int)std::min<size_t>((size_t)std::max(1u, std::thread::hardware_concurrency()),
+                                               std::min<size_t>((size_t)batch, work / 8192 + 1));
+    auto worker = [&](int w) {
+        for (int i = w; i < batch; i += nthreads)
+            item_tables(p, items[i], hx + (size_t)i * p->px, hy + (size_t)i * p->py, hp_items + i);
+    };
+    if (nthreads <= 1) {
+        worker(0);
+    } else {
+        std::vector<std::thread> pool;
+        for (int w = 1; w < nthreads; ++w) pool.emplace_back(worker, w);
+        worker(0);
+        for (auto& th : pool) th.join();
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(p->ix, hx, (size_t)batch * p->px * sizeof(float4), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(p->iy, hy, (size_t)batch * p->py * sizeof(float4), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(p->iprm, hp_items, (size_t)batch * sizeof(cwo::ItemParams), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaEventRecord(p->iev, s)))
+        return cuda_fail(e, "item table upload");
+    p->iev_pending = true;
+
+    cwo::HParams hpar{};
+    hpar.mode = cwo::HMODE_ASM_POLY;   // per item, see items
+    hpar.ax = p->ix; hpar.ay = p->iy; hpar.items = p->iprm;
+    hpar.x_item_stride = p->px; hpar.y_item_stride = p->py;
+    hpar.kbx = p->kb_x; hpar.kby = p->kb_y; hpar.pairs = p->pairs_x; hpar.npairs = p->px / 2 + 1;
+    const long long wstride = (long long)p->ny * p->px;
+    const float scale = (float)(1.0 / ((double)p->px * (double)p->py));
+    const bool timing = p->tev[0] != nullptr;
+    auto mark = [&](int i) { return timing ? cudaEventRecord(p->tev[i], s) : cudaSuccess; };
+    if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, (const float2*)in, in_stride, &p->wmap_f, 0, p->ny, batch, p->tw_x, s)) ||
+        (e = mark(1)))
+        return cuda_fail(e, "row forward launch");
+    if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, batch, p->tw_y, hpar, s)) || (e = mark(2)))
+        return cuda_fail(e, "column launch");
+    if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 0, (float2*)out, field, p->ny, batch, scale, p->tw_x, p->status, s)) ||
+        (e = mark(3)))
+        return cuda_fail(e, "row inverse launch");
+    return CWO_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
@@ -496,6 +624,11 @@ cwo_status cwo_propagate(cwo_plan* plan, const void* in_c64, void* out_c64, void
 cwo_status cwo_propagate_batch(cwo_plan* plan, const void* in, long long in_batch_stride, void* out,
                                int batch, const double* z_or_null, void* cuda_stream) {
     return run(plan, in, in_batch_stride, out, batch, z_or_null, cuda_stream, false);
+}
+
+cwo_status cwo_propagate_items(cwo_plan* plan, const void* in, long long in_batch_stride, void* out, int batch,
+                               const cwo_item* items, void* cuda_stream) {
+    return run_items(plan, in, in_batch_stride, out, batch, items, cuda_stream);
 }
 
 cwo_status cwo_propagate_adjoint(cwo_plan* plan, const void* in_c64, void* out_c64, void* cuda_stream) {

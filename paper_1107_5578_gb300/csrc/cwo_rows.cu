@@ -15,6 +15,8 @@
 // through a dense shared-memory tile [st][r]; the tile moves to and from the intermediate as TMA
 // tensor boxes of R rows x 256 columns (R * 8 contiguous bytes per column), so the transposed
 // global side costs the threads no load/store instructions.
+#include "cwo.h"
+#include "cwo_debug.h"
 #include "cwo_fft.cuh"
 #include "cwo_internal.h"
 #include "cwo_tma.cuh"
@@ -195,3 +197,38 @@ cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2
 }
 
 }  // namespace cwo
+
+// ------------------------------------------------------------------------------------------
+// Failure-path check of the bounded wait: one thread initialises an mbarrier for one arrival and,
+// unless `complete` is set, never arrives, so phase 0 never completes (a flag nothing sets); the
+// wait must give up after `limit` polls, set the timeout bit in the status word and return.
+// ------------------------------------------------------------------------------------------
+namespace {
+__global__ void k_debug_bounded_wait(unsigned limit, int complete, int* status) {
+    __shared__ __align__(8) uint64_t mbar;
+    cwo::mbar_init(&mbar, 1);
+    if (complete) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(cwo::smem_u32(&mbar)) : "memory");
+    cwo::mbar_wait_bounded(&mbar, 0, status, limit);
+}
+
+cwo_status debug_fail(cwo_status st, const char* msg) {
+    cwo::set_last_error(msg);
+    return st;
+}
+}  // namespace
+
+extern "C" cwo_status cwo_debug_bounded_wait(unsigned spin_limit, int complete, int* status_out) {
+    if (!status_out) return debug_fail(CWO_ERR_INVALID_ARG, "status_out is NULL");
+    if (spin_limit < 1 || spin_limit > (1u << 20)) return debug_fail(CWO_ERR_INVALID_ARG, "spin_limit must be in [1, 2^20]");
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        k_debug_bounded_wait<<<1, 1>>>(spin_limit, complete, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(status_out, d, sizeof(int), cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) return debug_fail(CWO_ERR_CUDA, cudaGetErrorString(e));
+    return CWO_OK;
+}

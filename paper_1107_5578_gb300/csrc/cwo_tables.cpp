@@ -12,6 +12,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
 
 #include "../../include/cwo.h"
 
@@ -81,31 +84,82 @@ std::vector<int> bin_table(const AxisGeo& g) {
     return b;
 }
 
-// FP64 Stockham radix-2 FFT, forward sign, out-of-place ping-pong
-void fft64(std::vector<cd>& x) {
-    const int n = (int)x.size();
-    std::vector<cd> y(n);
+// Per-length caches: twiddles W_P^j (j < P/2) of the FP64 FFT, and the axis-index lists of the
+// frequency pairs {+k, -k}.  Built once per length, shared by every thread (read-only after).
+namespace {
+struct AxisCache {
+    std::vector<double> wre, wim;        // W_P^j = exp(-2 pi i j / P), j < P/2
+    std::vector<int> kabs;               // |signed bin| of each axis index, 0 .. P/2
+    std::vector<int> first, second;      // for |k| = 0 .. P/2: the axis indices of +k and -k
+};
+std::mutex g_cache_mu;
+std::map<int, std::unique_ptr<AxisCache>> g_cache;
+
+const AxisCache& axis_cache(int P) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto& slot = g_cache[P];
+    if (!slot) {
+        auto c = std::make_unique<AxisCache>();
+        c->wre.resize(P / 2);
+        c->wim.resize(P / 2);
+        for (int j = 0; j < P / 2; ++j) {
+            const double ang = -2.0 * kPi * (double)j / (double)P;
+            c->wre[j] = std::cos(ang);
+            c->wim[j] = std::sin(ang);
+        }
+        const AxisGeo g(P);
+        c->kabs.resize(P);
+        c->first.assign(P / 2 + 1, -1);
+        c->second.assign(P / 2 + 1, -1);
+        for (int i = 0; i < P; ++i) {
+            const int k = std::abs(g.signed_bin(g.freq_of_idx(i)));
+            c->kabs[i] = k;
+            (c->first[k] < 0 ? c->first[k] : c->second[k]) = i;
+        }
+        slot = std::move(c);
+    }
+    return *slot;
+}
+}  // namespace
+
+// FP64 Stockham radix-2 FFT, forward sign, out-of-place ping-pong; real arithmetic written out
+// (no library complex multiply), twiddles from the per-length table
+void fft64(std::vector<cd>& xv) {
+    const int n = (int)xv.size();
+    const AxisCache& c = axis_cache(n);
+    std::vector<cd> yv(n);
+    double* x = reinterpret_cast<double*>(xv.data());
+    double* y = reinterpret_cast<double*>(yv.data());
     for (int l = n / 2, m = 1; l >= 1; l /= 2, m *= 2) {
         for (int j = 0; j < l; ++j) {
-            const double ang = -kPi * (double)j / (double)l;
-            const cd w(std::cos(ang), std::sin(ang));
+            const double wr = c.wre[(size_t)j * m], wi = c.wim[(size_t)j * m];   // W_{2l}^j = W_n^{j m}
+            const double* a = x + 2 * (size_t)j * m;
+            const double* b = x + 2 * ((size_t)j * m + (size_t)l * m);
+            double* o0 = y + 2 * (2 * (size_t)j * m);
+            double* o1 = o0 + 2 * (size_t)m;
             for (int k = 0; k < m; ++k) {
-                const cd c0 = x[k + j * m], c1 = x[k + j * m + l * m];
-                y[k + 2 * j * m] = c0 + c1;
-                y[k + 2 * j * m + m] = (c0 - c1) * w;
+                const double ar = a[2 * k], ai = a[2 * k + 1], br = b[2 * k], bi = b[2 * k + 1];
+                o0[2 * k] = ar + br;
+                o0[2 * k + 1] = ai + bi;
+                const double dr = ar - br, di = ai - bi;
+                o1[2 * k] = dr * wr - di * wi;
+                o1[2 * k + 1] = dr * wi + di * wr;
             }
         }
-        x.swap(y);
+        std::swap(x, y);
     }
+    if (x != reinterpret_cast<double*>(xv.data())) xv.swap(yv);
 }
 
 std::vector<cd> fresnel_axis_dft(int P, double pitch, double lambda, double z) {
     std::vector<cd> h(P);
     const double c = pitch * pitch / (2.0 * lambda * z);   // cycles per d^2
-    for (int i = 0; i < P; ++i) {
-        const double d = (double)(i < P / 2 ? i : i - P);
-        const double ph = frac01(c * d * d);
-        h[i] = cd(std::cos(2.0 * kPi * ph), std::sin(2.0 * kPi * ph));
+    // h(d) = h(-d): evaluate d = 0 .. P/2 and mirror
+    for (int d = 0; d <= P / 2; ++d) {
+        const double ph = frac01(c * (double)d * (double)d);
+        const cd v(std::cos(2.0 * kPi * ph), std::sin(2.0 * kPi * ph));
+        h[d] = v;
+        if (d > 0 && d < P / 2) h[P - d] = v;
     }
     fft64(h);
     return h;
@@ -126,15 +180,19 @@ void asm_axis_table(const AxisGeo& g, double pitch, double lambda, double z, boo
     const double Pd = (double)g.P * pitch;
     const double c1 = z * lambda / (2.0 * Pd * Pd);                              // K a / 2   per kt^2
     const double c2 = z * lambda * lambda * lambda / (8.0 * Pd * Pd * Pd * Pd);  // K a^2 / 8 per kt^4
-    for (int i = 0; i < g.P; ++i) {
-        const double kt = (double)g.signed_bin(g.freq_of_idx(i));
+    // every entry depends on kt^2 only: evaluate |kt| = 0 .. P/2 once, store at both indices
+    const AxisCache& c = axis_cache(g.P);
+    for (int k = 0; k <= g.P / 2; ++k) {
+        const double kt = (double)k;
         const double k2 = kt * kt;
         const double a = lambda * lambda * k2 / (Pd * Pd);
         const double W = frac01(frac01(c1 * k2) + frac01(c2 * k2 * k2)) - c0;
         const double u = sgn * rt * a;
         const float uh = (float)u;
         const float ul = (float)(u - (double)uh);
-        out[i] = make_float4((float)a, (float)W, uh, ul);
+        const float4 v = make_float4((float)a, (float)W, uh, ul);
+        out[c.first[k]] = v;
+        if (c.second[k] >= 0) out[c.second[k]] = v;
     }
 }
 
@@ -157,22 +215,23 @@ void make_h_tables(int px, int py, double dx, double dy, double lambda, double z
     if (!fresnel) {
         asm_axis_table(gx, dx, lambda, z, true, ax);
         asm_axis_table(gy, dy, lambda, z, false, ay);
-        *kf = (float)(z / lambda);
+        if (kf) *kf = (float)(z / lambda);
     } else {
         const std::vector<cd> Hx = fresnel_axis_dft(px, dx, lambda, z);
-        const std::vector<cd> Hy = fresnel_axis_dft(py, dy, lambda, z);
+        const std::vector<cd> Hy = (py == px && dy == dx) ? Hx : fresnel_axis_dft(py, dy, lambda, z);
         const cd C = fresnel_coeff(dx, dy, lambda, z, literal_scale);
+        const double cr = C.real(), ci = C.imag();
         // h_F is even in d (the unpaired sample d = -P/2 contributes (-1)^k, also even), so
         // H[k] = H[P - k]; one representative per pair keeps the float tables exactly even
+        const AxisCache& cx = axis_cache(px);
         for (int i = 0; i < px; ++i) {
-            const int k = gx.freq_of_idx(i);
-            const cd v = C * Hx[std::min(k, (px - k) % px)];
-            hx[i] = make_float2((float)v.real(), (float)v.imag());
+            const cd h = Hx[cx.kabs[i]];
+            hx[i] = make_float2((float)(cr * h.real() - ci * h.imag()), (float)(cr * h.imag() + ci * h.real()));
         }
+        const AxisCache& cy = axis_cache(py);
         for (int i = 0; i < py; ++i) {
-            const int k = gy.freq_of_idx(i);
-            const cd v = Hy[std::min(k, (py - k) % py)];
-            hy[i] = make_float2((float)v.real(), (float)v.imag());
+            const cd h = Hy[cy.kabs[i]];
+            hy[i] = make_float2((float)h.real(), (float)h.imag());
         }
     }
 }

@@ -51,11 +51,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, unsigned parity) {
 // Wait for phase `parity` of the barrier with an iteration limit.  On expiry the status word gets
 // kStatusTimeout, the thread keeps waiting (again bounded) so that copies still in flight land
 // before the block can exit, and false is returned: the caller must not use the data.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, unsigned parity, int* status) {
-    for (unsigned i = 0; i < kMbarSpinLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, unsigned parity, int* status,
+                                                  unsigned limit = kMbarSpinLimit) {
+    for (unsigned i = 0; i < limit; ++i)
         if (mbar_try_wait(mbar, parity)) return true;
     if (status) atomicOr(status, kStatusTimeout);
-    for (unsigned i = 0; i < kMbarSpinLimit; ++i)
+    for (unsigned i = 0; i < limit; ++i)
         if (mbar_try_wait(mbar, parity)) break;
     return false;
 }

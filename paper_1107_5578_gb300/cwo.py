@@ -34,6 +34,12 @@ _lock = threading.Lock()
 _lib = None
 
 
+class Item(ctypes.Structure):
+    """cwo_item: one entry of a mixed batch (cwo_propagate_items)."""
+    _fields_ = [("z", ctypes.c_double), ("wavelength", ctypes.c_double), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("type", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
 class CwoError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         self.status = status
@@ -62,6 +68,7 @@ def lib() -> ctypes.CDLL:
                 "cwo_propagate_batch": ([vp, vp, ll, vp, i, dpp, vp], i),
                 "cwo_propagate_adjoint": ([vp, vp, vp, vp], i),
                 "cwo_propagate_adjoint_batch": ([vp, vp, ll, vp, i, dpp, vp], i),
+                "cwo_propagate_items": ([vp, vp, ll, vp, i, ctypes.POINTER(Item), vp], i),
                 "cwo_launches_per_call": ([vp], i),
                 "cwo_plan_check": ([vp], i),
                 "cwo_plan_set_timing_events": ([vp, ctypes.POINTER(ctypes.c_void_p)], i),
@@ -73,6 +80,7 @@ def lib() -> ctypes.CDLL:
                 "cwo_debug_asm_axis": ([i, d, d, d, i, vp], i),
                 "cwo_debug_emulate": ([i, i, d, d, d, d, i, u, i, vp, vp], i),
                 "cwo_debug_line_fft": ([i, i, vp, vp], i),
+                "cwo_debug_bounded_wait": ([u, i, ctypes.POINTER(ctypes.c_int)], i),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -208,6 +216,27 @@ class Plan:
         _check_field(x, self.nx, self.ny, "input", b)
         return self._batch(x, self.nx * self.ny, b, z, out, stream, adjoint)
 
+    def propagate_items(self, x, items, out=None, stream=None):
+        """Mixed batch [B][Ny][Nx]: item i propagated with items[i] = (type, z, wavelength, dx, dy)
+        given as dicts or Item structures; the plan supplies only the shape and resources."""
+        b = x.shape[0] if x.dim() == 3 else 1
+        _check_field(x, self.nx, self.ny, "input", b)
+        if len(items) != b:
+            raise ValueError(f"{len(items)} items for {b} fields")
+        arr = (Item * b)()
+        for k, it in enumerate(items):
+            if isinstance(it, Item):
+                arr[k] = it
+            else:
+                arr[k] = Item(float(it["z"]), float(it["wavelength"]), float(it["dx"]),
+                              float(it.get("dy", it["dx"])), int(it["type"]), int(it.get("flags", 0)))
+        out = self._out(x, (b,)) if out is None else out
+        _check_field(out, self.nx, self.ny, "output", b)
+        check(lib().cwo_propagate_items(self.handle, ctypes.c_void_p(x.data_ptr()), self.nx * self.ny,
+                                        ctypes.c_void_p(out.data_ptr()), b, arr, _stream_handle(stream)),
+              "cwo_propagate_items")
+        return out
+
     def propagate_stack(self, x, zs, out=None, stream=None):
         """One source [Ny][Nx] propagated to len(zs) planes in one batched call (shared spectrum)."""
         _check_field(x, self.nx, self.ny, "input", 1)
@@ -269,6 +298,15 @@ def twiddles(p: int):
     out = np.empty(max(nst - 1, 0) * p, dtype=np.complex64)
     check(lib().cwo_debug_twiddles(p, out.ctypes.data), "cwo_debug_twiddles")
     return out
+
+
+def debug_bounded_wait(spin_limit: int, complete: bool) -> int:
+    """Run the bounded mbarrier wait on the current device against a barrier that completes
+    (complete=True) or that nothing completes, and return the status word it left (bit 0 =
+    the wait gave up)."""
+    st = ctypes.c_int(-1)
+    check(lib().cwo_debug_bounded_wait(int(spin_limit), int(bool(complete)), ctypes.byref(st)), "cwo_debug_bounded_wait")
+    return st.value
 
 
 def asm_axis(p: int, pitch: float, wavelength: float, z: float, is_x: bool):
