@@ -26,9 +26,10 @@ cwo_status cwo_debug_axis_bins(int p, int* bins);
  * out_ri: 2p doubles (re, im interleaved), caller-owned. */
 cwo_status cwo_debug_fresnel_axis(int p, double pitch, double lambda, double z, double* out_ri);
 
-/* Inter-stage twiddle table of an axis of length p: (stages-1) blocks of p/2 float4, block s
- * holding the pair (W_{L_s}^{j (2kp+1)}, W_{L_s}^{j (2kp+2)}), j = t mod S_s, at [kp][t],
- * kp = 0..7, t = 0..p/16-1.  out_ri: 2 * (stages-1) * p floats. */
+/* Inter-stage twiddle table of an axis of length p: one block per radix-16 stage s but the last,
+ * of 8 S_s float4 (S_s = L_s / 16, L_s = p / 16^s), holding the pair
+ * (W_{L_s}^{j (2kp+1)}, W_{L_s}^{j (2kp+2)}) at [kp][j], kp = 0..7, j = 0..S_s-1; thread t of the
+ * FFT reads j = t mod S_s.  out_ri: 4 floats per float4, sum over the blocks (caller-owned). */
 cwo_status cwo_debug_twiddles(int p, float* out_ri);
 
 /* ASM per-axis table {a, W - c0, u_hi, u_lo} of an axis of length p (see cwo_cols.cu) in axis

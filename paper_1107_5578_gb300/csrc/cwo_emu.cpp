@@ -22,10 +22,10 @@ struct Regs { float2 v[16]; };
 
 template <int P, int S, bool INV>
 void emu_twiddle(std::vector<Regs>& R, const float4* tw) {
-    constexpr int T = Geo<P>::T;
+    constexpr int T = Geo<P>::T, SS = Geo<P>::stride(S);
     for (int t = 0; t < T; ++t)
         for (int k = 1; k < 16; ++k) {
-            const float4 q = tw[S * (P / 2) + ((k - 1) / 2) * T + t];
+            const float4 q = tw[Geo<P>::tw_off(S) + ((k - 1) / 2) * SS + (t & (SS - 1))];
             const float2 w = (k & 1) ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
             R[t].v[k] = INV ? cmulc(R[t].v[k], w) : cmul(R[t].v[k], w);
         }

@@ -36,6 +36,9 @@ struct Geo {
     static __host__ __device__ constexpr int radix(int s) { return s == NST - 1 ? RLAST : 16; }
     static __host__ __device__ constexpr int len(int s) { return P >> (4 * s); }
     static __host__ __device__ constexpr int stride(int s) { return len(s) / radix(s); }
+    // twiddle table: stage s < NST-1 owns 8 * stride(s) float4 starting at tw_off(s)
+    static __host__ __device__ constexpr int tw_off(int s) { return s <= 0 ? 0 : tw_off(s - 1) + 8 * stride(s - 1); }
+    static constexpr int TW_WORDS = tw_off(NST - 1);
     static_assert(P >= 32 && P <= 8192 && (P & (P - 1)) == 0, "P must be a power of two in [32, 8192]");
 };
 
@@ -234,19 +237,21 @@ __device__ __forceinline__ void exchange(float2* __restrict__ sm, int c, int t, 
 }
 
 // Inter-stage twiddles W_{L_s}^{(t % S_s) k'}, k' = 1..15, of stage s < NST-1.
-// TwTable: per stage a block of P/2 float4 laid out [kp][t], kp = 0..7, holding the pair
-//          (W^{j (2kp+1)}, W^{j (2kp+2)}): 8 coalesced 16-byte loads per thread and stage.
+// TwTable: per stage a block of 8 S_s float4 laid out [kp][j], kp = 0..7, j = t mod S_s, holding
+//          the pair (W^{j (2kp+1)}, W^{j (2kp+2)}): 8 16-byte loads per thread and stage.  Only
+//          the S_s distinct j are stored, so the table of P = 4096 is 34 KB, not 64 KB, and
+//          stays in L1 next to the transfer-function tables.
 template <int P>
 struct TwTable {
     const float4* __restrict__ tw;
     int t;
     template <int S, bool INV>
     __device__ __forceinline__ void apply(float2 (&v)[16]) const {
-        constexpr int T = Geo<P>::T;
-        const float4* base = tw + S * (P / 2) + t;
+        constexpr int SS = Geo<P>::stride(S);
+        const float4* base = tw + Geo<P>::tw_off(S) + (t & (SS - 1));
 #pragma unroll
         for (int kp = 0; kp < 8; ++kp) {
-            const float4 w = __ldg(base + kp * T);
+            const float4 w = __ldg(base + kp * SS);
             v[2 * kp + 1] = INV ? cmulc(v[2 * kp + 1], make_float2(w.x, w.y)) : cmul(v[2 * kp + 1], make_float2(w.x, w.y));
             if (kp < 7)
                 v[2 * kp + 2] = INV ? cmulc(v[2 * kp + 2], make_float2(w.z, w.w)) : cmul(v[2 * kp + 2], make_float2(w.z, w.w));
@@ -257,11 +262,11 @@ struct TwTable {
 // the same twiddles applied to two transforms held by the same thread (two columns)
 template <int P, int S, bool INV>
 __device__ __forceinline__ void twiddle2(float2 (&a)[16], float2 (&b)[16], const float4* __restrict__ tw, int t) {
-    constexpr int T = Geo<P>::T;
-    const float4* base = tw + S * (P / 2) + t;
+    constexpr int SS = Geo<P>::stride(S);
+    const float4* base = tw + Geo<P>::tw_off(S) + (t & (SS - 1));
 #pragma unroll
     for (int kp = 0; kp < 8; ++kp) {
-        const float4 w = __ldg(base + kp * T);
+        const float4 w = __ldg(base + kp * SS);
         const float2 w0 = make_float2(w.x, w.y), w1 = make_float2(w.z, w.w);
         a[2 * kp + 1] = INV ? cmulc(a[2 * kp + 1], w0) : cmul(a[2 * kp + 1], w0);
         b[2 * kp + 1] = INV ? cmulc(b[2 * kp + 1], w0) : cmul(b[2 * kp + 1], w0);
@@ -283,12 +288,12 @@ struct TwRegs {
     __device__ __forceinline__ void load(const float4* __restrict__ table, int tt) {
         tw = table;
         t = tt;
-        constexpr int T = Geo<P>::T;
 #pragma unroll
         for (int s = 0; s < NS; ++s)
 #pragma unroll
             for (int kp = 0; kp < 8; ++kp) {
-                const float4 q = __ldg(table + s * (P / 2) + kp * T + tt);
+                const int SS = Geo<P>::stride(s);
+                const float4 q = __ldg(table + Geo<P>::tw_off(s) + kp * SS + (tt & (SS - 1)));
                 w[s][2 * kp] = make_float2(q.x, q.y);
                 if (kp < 7) w[s][2 * kp + 1] = make_float2(q.z, q.w);
             }

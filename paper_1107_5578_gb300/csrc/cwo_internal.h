@@ -65,7 +65,7 @@ void set_last_error(const char* msg);
 // item_off is added to the item index.
 int row_block_rows(int px, bool inverse);
 cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap,
-                           int item_off, int ny, int items, const float4* tw, cudaStream_t st);
+                           int item_off, int ny, int items, const float4* tw, int* status, cudaStream_t st);
 cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
                            int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st);
 // column pass of a shared-source z-stack: one forward transform per column, `planes` outputs

@@ -32,7 +32,7 @@
 namespace {
 
 constexpr int kMaxP = 2 * CWO_NOALLOC_MAX_SIDE;
-constexpr int kMaxTw = 2 * (kMaxP / 2);                    // (stages - 1) * P/2 float4, stages <= 3
+constexpr int kMaxTw = cwo::Geo<kMaxP>::TW_WORDS;          // compact per-stage twiddle blocks
 
 static __device__ __align__(256) float2 g_scratch[(size_t)CWO_NOALLOC_MAX_SIDE * kMaxP];
 static __device__ __align__(256) float4 g_tw_x[kMaxTw];
@@ -147,19 +147,20 @@ __global__ void k_setup(AxisParams ax, AxisParams ay, double lambda, double z, f
         int* kb = a == 0 ? kbx : kby;
         int lg = 0;
         while ((1 << lg) < g.P) ++lg;
-        const int nst = (lg + 3) / 4, T = g.P / 16;
-        // twiddles: entry i of each stage block, laid out [kp][t]
-        if (i < g.P / 2) {
-            const int kp = i / T, t = i % T;
-            for (int s = 0; s + 1 < nst; ++s) {
-                const int L = g.P >> (4 * s), S = L / 16;
+        const int nst = (lg + 3) / 4;
+        // twiddles: entry i of each stage block, laid out [kp][j], j = t mod S_s (8 S_s entries)
+        for (int s = 0, off = 0; s + 1 < nst; ++s) {
+            const int L = g.P >> (4 * s), S = L / 16;
+            if (i < 8 * S) {
+                const int kp = i / S, j = i % S;
                 double re[2], im[2];
                 for (int h = 0; h < 2; ++h) {
-                    const long long jk = (long long)(t % S) * (2 * kp + 1 + h) % L;
+                    const long long jk = (long long)j * (2 * kp + 1 + h) % L;
                     sincospi(-2.0 * (double)jk / (double)L, &im[h], &re[h]);
                 }
-                tw[s * (g.P / 2) + kp * T + t] = make_float4((float)re[0], (float)im[0], (float)re[1], (float)im[1]);
+                tw[off + i] = make_float4((float)re[0], (float)im[0], (float)re[1], (float)im[1]);
             }
+            off += 8 * S;
         }
         const int k = dev_freq_of_idx(g.P, i);
         const int kt = k < g.P / 2 ? k : k - g.P;
@@ -238,7 +239,7 @@ extern "C" cwo_status cwo_propagate_asm_noalloc(int nx, int ny, double dx, doubl
     if (cwo::make_intermediate_map(&wmap_f, a.scratch, ny, px, 1, cwo::row_block_rows(px, false)) != cudaSuccess ||
         cwo::make_intermediate_map(&wmap_i, a.scratch, ny, px, 1, cwo::row_block_rows(px, true)) != cudaSuccess)
         return fail(CWO_ERR_CUDA, "tensor map of the fixed scratch");
-    if ((e = cwo::launch_row_fwd(px, fin, field, &wmap_f, 0, ny, 1, a.tw_x, s)) ||
+    if ((e = cwo::launch_row_fwd(px, fin, field, &wmap_f, 0, ny, 1, a.tw_x, a.status, s)) ||
         (e = cwo::launch_col(py, a.scratch, wstride, a.scratch, wstride, px, 1, a.tw_y, hp, s)) ||
         (e = cwo::launch_row_inv(px, &wmap_i, 0, fout, field, ny, 1, scale, a.tw_x, a.status, s)))
         return fail(CWO_ERR_CUDA, cudaGetErrorString(e));

@@ -111,7 +111,7 @@ cwo_status upload(T* dst, const std::vector<T>& src, const char* what) {
 size_t tables_bytes(int nx, int ny) {
     const AxisGeo gx(2 * nx), gy(2 * ny);
     size_t b = 0;
-    b += (size_t)std::max(gx.NST - 1, 0) * (gx.P / 2) * sizeof(float4) + (size_t)std::max(gy.NST - 1, 0) * (gy.P / 2) * sizeof(float4);
+    b += (size_t)(gx.tw_off(gx.NST - 1) + gy.tw_off(gy.NST - 1)) * sizeof(float4);
     b += (size_t)(gx.P + gy.P) * sizeof(int);
     b += (size_t)(gx.P + gy.P) * sizeof(float4) + sizeof(float) * 2;
     return b;
@@ -383,7 +383,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         // the shared source: row pass once, then per-plane column and inverse row passes
         float2* w0 = p->scratch;
         float2* wz = p->scratch + wstride;
-        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, 0, &p->wmap_f, 0, p->ny, 1, p->tw_x, s)) || (e = mark(1)))
+        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, 0, &p->wmap_f, 0, p->ny, 1, p->tw_x, p->status, s)) || (e = mark(1)))
             return cuda_fail(e, "row forward launch");
         if (per_item_k) {
             for (int i = 0; i < batch; ++i) {
@@ -399,7 +399,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
             return cuda_fail(e, "row inverse launch");
     } else {
         const long long istr = in_stride ? in_stride : field;
-        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, istr, &p->wmap_f, 0, p->ny, batch, p->tw_x, s)) || (e = mark(1)))
+        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, istr, &p->wmap_f, 0, p->ny, batch, p->tw_x, p->status, s)) || (e = mark(1)))
             return cuda_fail(e, "row forward launch");
         if (per_item_k) {
             for (int i = 0; i < batch; ++i) {
@@ -526,7 +526,7 @@ cwo_status run_items(cwo_plan* p, const void* in, long long in_stride, void* out
     const float scale = (float)(1.0 / ((double)p->px * (double)p->py));
     const bool timing = p->tev[0] != nullptr;
     auto mark = [&](int i) { return timing ? cudaEventRecord(p->tev[i], s) : cudaSuccess; };
-    if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, (const float2*)in, in_stride, &p->wmap_f, 0, p->ny, batch, p->tw_x, s)) ||
+    if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, (const float2*)in, in_stride, &p->wmap_f, 0, p->ny, batch, p->tw_x, p->status, s)) ||
         (e = mark(1)))
         return cuda_fail(e, "row forward launch");
     if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, batch, p->tw_y, hpar, s)) || (e = mark(2)))

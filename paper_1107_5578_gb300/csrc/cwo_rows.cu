@@ -15,6 +15,8 @@
 // through a dense shared-memory tile [st][r]; the tile moves to and from the intermediate as TMA
 // tensor boxes of R rows x 256 columns (R * 8 contiguous bytes per column), so the transposed
 // global side costs the threads no load/store instructions.
+#include <algorithm>
+
 #include "cwo.h"
 #include "cwo_debug.h"
 #include "cwo_fft.cuh"
@@ -98,21 +100,113 @@ k_row_inv(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __rest
     for (int e = 0; e < 8; ++e) dst[t + e * T] = cscale(v[e], scale);   // crop: first Nx outputs
 }
 
+// ------------------------------------------------------------------------------------------
+// Persistent row passes: one CTA per SM (or as many as fit) walks groups g = blockIdx.x,
+// + gridDim.x, ... of R rows, so that the memory traffic of one group overlaps the FFT of another.
+//
+// Forward: the R input rows of the NEXT group are copied into a staging buffer by the bulk-copy
+// engine (one contiguous copy per row, completion on an mbarrier) while the current group is
+// transformed; the transposed tile of a group is written out by TMA stores that drain while the
+// next group's input is read from the staging buffer.  Shared memory: exchange region / tile
+// (row_smem_words), staging R x (N + 4) (row stride padded so the r-fast reads hit distinct
+// banks), one mbarrier.
+// ------------------------------------------------------------------------------------------
+template <int P, int R>
+__host__ __device__ constexpr int stage_stride() { return P / 2 + 4; }
+
+template <int P, int R>
+__host__ __device__ constexpr size_t row_fwd_p_smem_bytes() {
+    return (row_smem_words<P, R>() + (size_t)R * stage_stride<P, R>()) * sizeof(float2) + sizeof(uint64_t);
+}
+
+template <int P, int R>
+__global__ void __launch_bounds__(R * (P / 16), 1)
+k_row_fwd_p(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap wmap,
+            int item_off, int groups_per_item, int total_groups, const float4* __restrict__ tw, int* status) {
+    constexpr int T = P / 16, N = P / 2, NT = R * T, SST = stage_stride<P, R>();
+    constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
+    extern __shared__ __align__(1024) float2 sm[];
+    float2* stage = sm + row_smem_words<P, R>();
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(stage + R * SST);
+    const int r = threadIdx.x % R, t = threadIdx.x / R;
+    auto issue = [&](int g) {   // thread 0: the R rows of group g into the staging buffer
+        const int item = g / groups_per_item, y0 = (g % groups_per_item) * R;
+        const float2* src = in + item * in_item_stride + (long long)y0 * N;
+        mbar_arrive_expect_tx(mbar, (unsigned)(R * N * sizeof(float2)));
+#pragma unroll 1
+        for (int rr = 0; rr < R; ++rr) bulk_load(stage + rr * SST, src + rr * N, (unsigned)(N * sizeof(float2)), mbar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        if ((int)blockIdx.x < total_groups) issue(blockIdx.x);
+    }
+    __syncthreads();
+    unsigned parity = 0;
+#pragma unroll 1
+    for (int g = blockIdx.x; g < total_groups; g += gridDim.x, parity ^= 1u) {
+        const bool ok = mbar_wait_bounded(mbar, parity, status);
+        float2 v[16];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = stage[r * SST + t + e * T];   // DIF stage-0 positions t + e P/16
+#pragma unroll
+        for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);      // zero padding, never loaded
+        if (threadIdx.x == 0) tma_store_wait_read();                     // previous tile read out
+        fence_proxy_async_smem();   // these reads of the staging buffer precede the next bulk copy into it
+        if (__syncthreads_or(!ok)) break;                                // a copy did not land
+        if (threadIdx.x == 0 && g + (int)gridDim.x < total_groups) issue(g + gridDim.x);
+        fwd_from<P, R, PadLayout<P, R>, 0, 8, 0>(v, sm, r, t, TwTable<P>{tw, t});
+#pragma unroll
+        for (int e = 0; e < 16; ++e) sm[e * NT + threadIdx.x] = v[e];
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int item = g / groups_per_item, y0 = (g % groups_per_item) * R;
+#pragma unroll 1
+            for (int b = 0; b < P / BOX; ++b) tma_store_3d(&wmap, sm + b * BOX * R, y0, b * BOX, item + item_off);
+            tma_store_commit();
+        }
+    }
+    if (threadIdx.x == 0) tma_store_wait_read();
+}
+
 template <typename K>
 static cudaError_t ensure_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// CTAs of a persistent launch: resident CTAs per SM x SMs, at most one per group
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, int groups) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        return 0;
+    return std::min(groups, sms * per_sm);
+}
+
 template <int P>
 static cudaError_t row_fwd_impl(const float2* in, long long in_item_stride, const CUtensorMap* wmap,
-                                int item_off, int ny, int items, const float4* tw, cudaStream_t st) {
+                                int item_off, int ny, int items, const float4* tw, int* status, cudaStream_t st) {
     constexpr int R = rows_fwd<P>();
     constexpr int T = P / 16;
+    if (ny % R) return cudaErrorInvalidValue;
+    // persistent pipelined kernel where its bulk copies are legal: rows start on 16-byte boundaries
+    const bool aligned = ((uintptr_t)in % 16 == 0) && (in_item_stride % 2 == 0);
+    if (P >= 512 && aligned) {
+        const size_t smem = row_fwd_p_smem_bytes<P, R>();
+        cudaError_t e = ensure_smem(k_row_fwd_p<P, R>, smem);
+        if (e != cudaSuccess) return e;
+        const int groups = (ny / R) * items;
+        const int grid = persistent_grid(k_row_fwd_p<P, R>, R * T, smem, groups);
+        if (grid > 0) {
+            k_row_fwd_p<P, R><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, ny / R, groups, tw, status);
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = row_smem_words<P, R>() * sizeof(float2);
     cudaError_t e = ensure_smem(k_row_fwd<P, R>, smem);
     if (e != cudaSuccess) return e;
-    if (ny % R) return cudaErrorInvalidValue;
     dim3 grid(ny / R, items);
     k_row_fwd<P, R><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, tw);
     return cudaGetLastError();
@@ -124,9 +218,9 @@ static cudaError_t row_inv_impl(const CUtensorMap* wmap, int item_off, float2* o
     constexpr int R = rows_inv<P>();
     constexpr int T = P / 16;
     const size_t smem = row_smem_words<P, R>() * sizeof(float2) + sizeof(uint64_t);   // tile + mbarrier
+    if (ny % R) return cudaErrorInvalidValue;
     cudaError_t e = ensure_smem(k_row_inv<P, R>, smem);
     if (e != cudaSuccess) return e;
-    if (ny % R) return cudaErrorInvalidValue;
     dim3 grid(ny / R, items);
     k_row_inv<P, R><<<grid, R * T, smem, st>>>(*wmap, item_off, out, out_item_stride, scale, tw, status);
     return cudaGetLastError();
@@ -177,9 +271,9 @@ int row_block_rows(int px, bool inverse) {
 }
 
 cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap,
-                           int item_off, int ny, int items, const float4* tw, cudaStream_t st) {
+                           int item_off, int ny, int items, const float4* tw, int* status, cudaStream_t st) {
     switch (px) {
-#define CASE(P) case P: return row_fwd_impl<P>(in, in_item_stride, wmap, item_off, ny, items, tw, st);
+#define CASE(P) case P: return row_fwd_impl<P>(in, in_item_stride, wmap, item_off, ny, items, tw, status, st);
         CWO_P_CASES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;

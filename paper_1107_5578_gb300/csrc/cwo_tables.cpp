@@ -48,21 +48,21 @@ int AxisGeo::freq_of_pos(int pos) const {
 }
 
 std::vector<float4> twiddle_table(const AxisGeo& g) {
-    // per radix-16 stage s: P/2 float4 laid out [kp][t], kp = 0..7, holding
-    // (W_L^{j (2kp+1)}, W_L^{j (2kp+2)}), j = t mod S_s, L = L_s
-    std::vector<float4> tw((size_t)(g.NST > 1 ? g.NST - 1 : 0) * (g.P / 2));
+    // per radix-16 stage s (all but the last): 8 S_s float4 laid out [kp][j], kp = 0..7,
+    // j = 0..S_s-1 (= t mod S_s), holding (W_L^{j (2kp+1)}, W_L^{j (2kp+2)}), L = L_s
+    std::vector<float4> tw((size_t)g.tw_off(g.NST - 1));
     for (int s = 0; s + 1 < g.NST; ++s) {
         const int L = g.len(s), S = g.stride(s);
         for (int kp = 0; kp < 8; ++kp)
-            for (int t = 0; t < g.T; ++t) {
+            for (int j = 0; j < S; ++j) {
                 double re[2], im[2];
                 for (int h = 0; h < 2; ++h) {
-                    const long long jk = (long long)(t % S) * (2 * kp + 1 + h) % L;
+                    const long long jk = (long long)j * (2 * kp + 1 + h) % L;
                     const double ang = -2.0 * kPi * (double)jk / (double)L;
                     re[h] = std::cos(ang);
                     im[h] = std::sin(ang);
                 }
-                tw[(size_t)s * (g.P / 2) + (size_t)kp * g.T + t] =
+                tw[(size_t)g.tw_off(s) + (size_t)kp * S + j] =
                     make_float4((float)re[0], (float)im[0], (float)re[1], (float)im[1]);
             }
     }

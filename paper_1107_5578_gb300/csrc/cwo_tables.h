@@ -18,6 +18,7 @@ struct AxisGeo {
     int radix(int s) const { return s == NST - 1 ? RLAST : 16; }
     int len(int s) const { return P >> (4 * s); }
     int stride(int s) const { return len(s) / radix(s); }
+    int tw_off(int s) const { return s <= 0 ? 0 : tw_off(s - 1) + 8 * stride(s - 1); }   // float4 units
     int freq_of_pos(int pos) const;   // bin whose forward DIF output lands at position pos
     int freq_of_idx(int idx) const { return freq_of_pos(16 * (idx % T) + idx / T); }
     int signed_bin(int k) const { return k < P / 2 ? k : k - P; }

@@ -293,9 +293,12 @@ def fresnel_axis(p: int, pitch: float, wavelength: float, z: float):
 
 
 def twiddles(p: int):
+    """Inter-stage twiddle table of an axis of length p as complex64: per stage s the block
+    [kp][j] of (W^{j(2kp+1)}, W^{j(2kp+2)}) pairs, j < S_s = (p >> 4s) / 16."""
     import numpy as np
     nst = (int(p).bit_length() - 1 + 3) // 4
-    out = np.empty(max(nst - 1, 0) * p, dtype=np.complex64)
+    words = sum(8 * ((p >> (4 * s)) // 16) for s in range(max(nst - 1, 0)))
+    out = np.empty(2 * words, dtype=np.complex64)
     check(lib().cwo_debug_twiddles(p, out.ctypes.data), "cwo_debug_twiddles")
     return out
 

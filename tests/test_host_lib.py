@@ -104,19 +104,20 @@ def test_axis_bins_are_a_permutation_matching_the_line_fft(lib, p):
 
 @pytest.mark.parametrize("p", [32, 256, 4096, 8192])
 def test_twiddle_tables(lib, p):
-    tw = cwo.twiddles(p)          # complex64 view: per stage [kp][t] pairs (k = 2kp+1, 2kp+2)
-    T = p // 16
+    tw = cwo.twiddles(p)          # complex64 view: per stage [kp][j] pairs (k = 2kp+1, 2kp+2)
     nst = (p.bit_length() - 1 + 3) // 4
-    L = p
+    L, off = p, 0
     for s in range(nst - 1):
-        S = L // 16
-        blk = tw[s * p:(s + 1) * p].reshape(8, T, 2)
-        t = np.arange(T)[None, :]
+        S = L // 16                # thread t uses j = t mod S
+        blk = tw[off:off + 16 * S].reshape(8, S, 2)
+        j = np.arange(S)[None, :]
         for h in range(2):
             k = (2 * np.arange(8) + 1 + h)[:, None]
-            want = np.exp(-2j * np.pi * ((t % S) * k % L) / L)
+            want = np.exp(-2j * np.pi * (j * k % L) / L)
             assert np.max(np.abs(blk[:, :, h] - want)) < 1e-7
+        off += 16 * S
         L //= 16
+    assert off == len(tw)
 
 
 @pytest.mark.parametrize("p,pitch,lam,z", [(64, 10e-6, 633e-9, 0.05), (512, 8e-6, 532e-9, -0.3)])
