@@ -234,7 +234,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_1107_5578_gb300 import cwo, synth
+    from paper_1107_5578_gb300 import cwo, replicas, synth
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -244,7 +244,7 @@ def main():
     plan = cwo.Plan(N, N, PITCH, PITCH, LAM, Z, cwo.ANGULAR)
     plan.reserve(B)
     # synthetic inputs: B random fields per rank (amplitude U[0,1), phase U[0, 2 pi))
-    base = torch.from_numpy(synth.random_field(N, seed=1000 + rank).astype(np.complex64))
+    base = torch.from_numpy(synth.random_field(N, seed=replicas.rank_seed(1000, rank)).astype(np.complex64))
     g = torch.Generator(device="cpu").manual_seed(rank)
     host_in = torch.empty((B, N, N), dtype=torch.complex64).pin_memory()
     for i in range(B):
@@ -282,14 +282,9 @@ def main():
         wall1 = time.perf_counter()
     plan.set_timing_events(None)
     clocks = clk.summary()
-    ms_total = t_start.elapsed_time(t_end)
-    t = torch.tensor([ms_total], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total = float(t.item())
+    ms_total = replicas.max_over_ranks(t_start.elapsed_time(t_end), dev)
     ms_step = ms_total / args.steps
-    props = B * args.steps * world
-    value = props / (ms_total / 1e3)
+    value = replicas.job_rate(B * args.steps, world, ms_total / 1e3)
 
     # per-pass averages (ms per launch) and roofline of the dominant pass
     pp = per_pass / args.steps
@@ -316,11 +311,8 @@ def main():
         host_out.copy_(y, non_blocking=True)
     e1.record(stream)
     barrier()
-    e_ms = e0.elapsed_time(e1)
-    te = torch.tensor([e_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e_value = B * e_steps * world / (float(te.item()) / 1e3)
+    e_ms = replicas.max_over_ranks(e0.elapsed_time(e1), dev)
+    e_value = replicas.job_rate(B * e_steps, world, e_ms / 1e3)
 
     stack = stack_measurement(dev, peaks()[0])
     serve = serving_measurement(dev, args.serving_requests, args.serving_rate) \
