@@ -15,6 +15,10 @@ Pins (each checked by the ``-m "not gpu"`` tests, none of them by re-calling thi
                           Gaussian-beam Hankel quadrature, Parseval, z then -z
   * adjoint flag       -- dot-product test <A x, y> = <x, A^H y>
   * ``hologram_grad``  -- central finite differences
+  * ``gs_run``         -- z = 0 fixed point, zero iterations = one propagation plus the phase
+                          constraint, unit-amplitude kinoform, and on the circular (unitary)
+                          grid the error-reduction property: the object-plane amplitude error
+                          never increases from one iteration to the next
 """
 from __future__ import annotations
 
@@ -175,3 +179,48 @@ def hologram_loss_grad(phi, canvas: tuple, offset: tuple, target, dx: float, lam
     back = propagate(g, dx, dx, lam, z, ANGULAR, ADJOINT)
     grad = 2.0 * np.real(-1j * np.conj(x[oy:oy + h, ox:ox + w]) * back[oy:oy + h, ox:ox + w])
     return loss, grad
+
+
+def phase_only(u) -> np.ndarray:
+    """The phase constraint of the GS iteration: keep the phase, set the amplitude to one
+    (a pixel of zero amplitude has phase 0, i.e. becomes 1).  Section "GS algorithm"."""
+    u = _c128(u)
+    m = np.abs(u)
+    out = np.ones_like(u)
+    nz = m > 0
+    out[nz] = u[nz] / m[nz]
+    return out
+
+
+def gs_run(amplitude, field0, dx: float, dy: float, lam: float, z: float, iterations: int,
+           flags: int = 0):
+    """Gerchberg-Saxton kinoform iteration with the angular spectrum method, in the order of
+    Section "GS algorithm": propagate the object field (amplitude with its initial phase) by +z
+    and keep the phase (kinoform); then, per iteration, propagate the kinoform by -z, replace
+    the amplitude by the object amplitude (amplitude constraint), propagate by +z and keep the
+    phase (phase constraint).  Returns (kinoform, reconstructed intensity |ASM(-z) kinoform|^2).
+    ``flags`` is passed to every propagation (NO_PAD gives the circular, unitary variant)."""
+    a1 = np.asarray(amplitude, dtype=np.float64)
+    u = phase_only(propagate(field0, dx, dy, lam, z, ANGULAR, flags))
+    for _ in range(int(iterations)):
+        back = propagate(u, dx, dy, lam, -z, ANGULAR, flags)
+        obj = a1 * phase_only(back)
+        u = phase_only(propagate(obj, dx, dy, lam, z, ANGULAR, flags))
+    rec = propagate(u, dx, dy, lam, -z, ANGULAR, flags)
+    return u, np.abs(rec) ** 2
+
+
+def gs_amplitude_errors(amplitude, field0, dx: float, dy: float, lam: float, z: float,
+                        iterations: int, flags: int = 0) -> np.ndarray:
+    """|| |ASM(-z) kinoform_k| - amplitude || after k = 0 .. iterations GS iterations (the
+    object-plane error of the error-reduction view of the iteration)."""
+    a1 = np.asarray(amplitude, dtype=np.float64)
+    errs = []
+    u = phase_only(propagate(field0, dx, dy, lam, z, ANGULAR, flags))
+    for k in range(int(iterations) + 1):
+        back = propagate(u, dx, dy, lam, -z, ANGULAR, flags)
+        errs.append(float(np.linalg.norm(np.abs(back) - a1)))
+        if k == iterations:
+            break
+        u = phase_only(propagate(a1 * phase_only(back), dx, dy, lam, z, ANGULAR, flags))
+    return np.array(errs)

@@ -14,6 +14,9 @@ are not available, so these stand in for them):
   * hologram_problem     phase ~ U[0, 2 pi) on 1080 x 1920 plus a smooth target made of 20
                          random Gaussians (phase-only hologram optimisation)
   * serving_requests     Poisson arrivals with mixed N, type, z, wavelength and pitch
+  * gs_problem           GS kinoform input: amplitude sqrt(I) of a smooth test image I in
+                         [0, 1] (30 Gaussians, sigma ~ U[N/64, N/8], peaks ~ U[0.3, 1], plus
+                         two bright bars) and the initial random phase U[0, 2 pi)
   * gaussian_beam        exp(-r^2 / w0^2) about a given centre (closed-form test beam)
 """
 from __future__ import annotations
@@ -92,3 +95,21 @@ def serving_requests(n_req: int, seed: int, rate_hz: float = 2000.0,
     pitch = 4e-6 + 6e-6 * g.random(n_req)
     pool = g.integers(0, 1 << 30, size=n_req)
     return {"t": t, "n": n, "kind": kind, "z": z, "lam": lam, "pitch": pitch, "pool": pool}
+
+
+def gs_problem(n: int, seed: int, n_gauss: int = 30):
+    """(amplitude [n][n] >= 0, field0 = amplitude * exp(i phase0)) for the GS kinoform loop."""
+    g = rng(seed)
+    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)
+    img = np.zeros((n, n))
+    for _ in range(n_gauss):
+        cy, cx = g.random() * n, g.random() * n
+        s = n / 64.0 + (n / 8.0 - n / 64.0) * g.random()
+        a = 0.3 + 0.7 * g.random()
+        img += a * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2.0 * s * s))
+    img[n // 4:n // 4 + max(1, n // 32), n // 8:7 * n // 8] += 1.0
+    img[n // 8:7 * n // 8, 3 * n // 4:3 * n // 4 + max(1, n // 32)] += 1.0
+    img /= img.max()
+    amp = np.sqrt(img)
+    phase0 = g.random((n, n)) * (2.0 * np.pi)
+    return amp, amp * np.exp(1j * phase0)

@@ -268,3 +268,53 @@ def test_rejects_bad_arguments():
         oracle.propagate(np.ones((8, 12), complex), PITCH, PITCH, LAM, 0.1)
     with pytest.raises(ValueError):
         oracle.propagate(u, -PITCH, PITCH, LAM, 0.1)
+
+
+# ---------------------------------------------------------------------------------------------
+# GS kinoform iteration (Section "GS algorithm")
+# ---------------------------------------------------------------------------------------------
+def test_gs_zero_distance_is_a_fixed_point():
+    # ASM at z = 0 is the identity, so the kinoform is the phase of the initial field, the
+    # amplitude and phase constraints leave it unchanged, and the reconstruction is |1|^2
+    amp, f0 = synth.gs_problem(32, seed=4)
+    kin, inten = oracle.gs_run(amp, f0, 8e-6, 8e-6, 532e-9, 0.0, iterations=3)
+    assert np.max(np.abs(kin - np.exp(1j * np.angle(f0)))) < 1e-12
+    assert np.max(np.abs(inten - 1.0)) < 1e-12
+
+
+def test_gs_zero_iterations_is_one_propagation_and_the_phase():
+    amp, f0 = synth.gs_problem(32, seed=5)
+    kin, inten = oracle.gs_run(amp, f0, 8e-6, 8e-6, 532e-9, 0.01, iterations=0)
+    u = np.fft.ifft2(np.fft.fft2(np.pad(f0, ((0, 32), (0, 32)))) *
+                     oracle.asm_transfer(64, 64, 8e-6, 8e-6, 532e-9, 0.01))[:32, :32]
+    assert np.max(np.abs(kin - u / np.abs(u))) < 1e-10
+    r = np.fft.ifft2(np.fft.fft2(np.pad(kin, ((0, 32), (0, 32)))) *
+                     oracle.asm_transfer(64, 64, 8e-6, 8e-6, 532e-9, -0.01))[:32, :32]
+    assert np.max(np.abs(inten - np.abs(r) ** 2)) < 1e-10
+
+
+def test_gs_kinoform_has_unit_amplitude():
+    amp, f0 = synth.gs_problem(64, seed=6)
+    kin, _ = oracle.gs_run(amp, f0, 8e-6, 8e-6, 532e-9, 0.02, iterations=4)
+    assert np.max(np.abs(np.abs(kin) - 1.0)) < 1e-13
+
+
+def test_gs_error_never_increases_on_the_unitary_grid():
+    # with circular (unpadded) ASM and no evanescent band the propagation is unitary, and the
+    # iteration is an alternating projection: the object-plane amplitude error is non-increasing
+    amp, f0 = synth.gs_problem(64, seed=7)
+    errs = oracle.gs_amplitude_errors(amp, f0, 8e-6, 8e-6, 532e-9, 0.02, iterations=12, flags=oracle.NO_PAD)
+    assert np.all(np.diff(errs) <= 1e-9 * errs[0])
+    assert errs[-1] < 0.95 * errs[0]
+
+
+def test_gs_planted_amplitude_error_is_caught():
+    # a mistake planted in the amplitude constraint (squared amplitude instead of amplitude)
+    # breaks the fixed point of the z = 0 case
+    amp, f0 = synth.gs_problem(32, seed=4)
+    wrong_amp = amp ** 2
+    _, inten = oracle.gs_run(wrong_amp, f0, 8e-6, 8e-6, 532e-9, 0.0, iterations=1)
+    assert np.max(np.abs(inten - 1.0)) < 1e-12        # intensity of a kinoform: still 1 at z = 0
+    errs_ok = oracle.gs_amplitude_errors(amp, f0, 8e-6, 8e-6, 532e-9, 0.0, 1)
+    errs_bad = oracle.gs_amplitude_errors(wrong_amp, f0, 8e-6, 8e-6, 532e-9, 0.0, 1)
+    assert np.all(errs_ok > 0) and not np.allclose(errs_ok, errs_bad)
