@@ -215,6 +215,36 @@ def serving_measurement(dev, n_req, rate_hz):
             "continuous": cont, "serial": ser}
 
 
+# Table "Calculation times of the GS algorithm on the CPU and GPUs", 40 iterations, GeForce GTX580
+GS_PAPER_MS_40 = {512: 338.0, 1024: 1.19e3, 2048: 4.65e3}
+
+
+def gs_measurement(dev, iterations=40):
+    """GS kinoform loop (Section "GS algorithm"): object = sqrt of a synthetic test image with a
+    random phase, ASM at +-0.1 m, 633 nm, 10 um; the timed region covers the first propagation,
+    `iterations` iterations and the final reconstruction (2 * iterations + 2 propagations), as
+    the paper times its loop, with everything resident on the device."""
+    import torch
+    from paper_1107_5578_gb300 import gs
+    out = []
+    for n in (512, 1024, 2048):
+        prob = gs.GSProblem(n, seed=1, device=dev)
+        prob.run(2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, inten = prob.run(iterations)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out.append({"n": n, "iterations": iterations, "ms": round(ms, 3),
+                    "propagations_per_s": round((2 * iterations + 2) / (ms / 1e3), 1),
+                    "amplitude_error": round(gs.amplitude_error(inten, prob.amplitude), 5),
+                    "paper_gtx580_ms": GS_PAPER_MS_40[n]})
+        prob.plan.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,6 +345,7 @@ def main():
     e_value = replicas.job_rate(B * e_steps, world, e_ms / 1e3)
 
     stack = stack_measurement(dev, peaks()[0])
+    gs_res = gs_measurement(dev) if rank == 0 else None
     serve = serving_measurement(dev, args.serving_requests, args.serving_rate) \
         if args.serving_requests > 0 and rank == 0 else None
     if world > 1:
@@ -343,6 +374,7 @@ def main():
                 "h2d_bytes_per_step": B * N * N * 8, "d2h_bytes_per_step": B * N * N * 8},
         "gpu_launches": plan.launches_per_call * args.steps,
         "fresnel_stack": stack,
+        "gs_kinoform": gs_res,
         "serving": serve,
         "wall_s": round(wall1 - wall0, 3),
         "cpu_baseline": cpu,

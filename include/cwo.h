@@ -161,6 +161,36 @@ cwo_status cwo_propagate_adjoint_batch(cwo_plan* plan, const void* in, long long
                                        void* out, int batch, const double* z_or_null,
                                        void* cuda_stream);
 
+/* Output epilogues, fused into the last pass of a propagation (the constraints of the
+ * Gerchberg-Saxton iteration, Section "GS algorithm"; w is the propagated value of a pixel):
+ *   CWO_EPI_NONE       out = w
+ *   CWO_EPI_PHASE      out = w / |w|           phase constraint; a zero pixel becomes 1
+ *   CWO_EPI_AMPLITUDE  out = a w / |w|         amplitude constraint with the pixel's a >= 0
+ *   CWO_EPI_INTENSITY  intensity = |w|^2       reconstruction; out is not written */
+typedef enum { CWO_EPI_NONE = 0, CWO_EPI_PHASE = 1, CWO_EPI_AMPLITUDE = 2, CWO_EPI_INTENSITY = 3 } cwo_epilogue;
+
+/* One propagation of `batch` contiguous fields [batch][ny][nx] (forward, or the adjoint conj(H),
+ * which for the angular spectrum method is the propagation by -z), followed by an epilogue.
+ * amplitude (CWO_EPI_AMPLITUDE) and intensity (CWO_EPI_INTENSITY) are float [batch][ny][nx]
+ * device buffers owned by the caller; out_c64 may be NULL with CWO_EPI_INTENSITY.  in and out may
+ * alias.  Errors as cwo_propagate_batch; CWO_ERR_INVALID_ARG for a missing or short buffer. */
+cwo_status cwo_propagate_epilogue(cwo_plan* plan, const void* in_c64, void* out_c64, int batch, int adjoint,
+                                  int epilogue, const float* amplitude, float* intensity, void* cuda_stream);
+
+/* Gerchberg-Saxton kinoform iteration (Section "GS algorithm") with an angular-spectrum plan of
+ * distance z, on `batch` independent fields at once, all stream-ordered on cuda_stream:
+ *   field <- phase(ASM(+z) field)                                    (the kinoform)
+ *   repeat `iterations` times:
+ *     field <- amplitude * phase(ASM(-z) field)                      (amplitude constraint)
+ *     field <- phase(ASM(+z) field)                                  (phase constraint)
+ *   intensity <- |ASM(-z) field|^2                                   (if intensity != NULL)
+ * field_c64 (in: the object field, amplitude times its initial phase; out: the kinoform),
+ * amplitude and intensity are [batch][ny][nx] device buffers of the caller.  Each propagation is
+ * the three-pass path with the constraint fused into its last pass (6 launches per iteration).
+ * CWO_ERR_UNSUPPORTED for a Fresnel plan, CWO_ERR_INVALID_ARG for bad arguments. */
+cwo_status cwo_gs_run(cwo_plan* plan, const float* amplitude, void* field_c64, float* intensity, int batch,
+                      int iterations, void* cuda_stream);
+
 /* Number of kernel launches one call of cwo_propagate_batch makes for this plan (for launch
  * accounting in benchmarks). */
 int cwo_launches_per_call(const cwo_plan* plan);

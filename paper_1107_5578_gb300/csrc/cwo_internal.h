@@ -66,8 +66,16 @@ void set_last_error(const char* msg);
 int row_block_rows(int px, bool inverse);
 cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap,
                            int item_off, int ny, int items, const float4* tw, int* status, cudaStream_t st);
+// output epilogue of the inverse row pass (see cwo_rows.cu); amp / inten are [items][Ny][Nx]
+enum EpiMode { EPI_NONE = 0, EPI_PHASE = 1, EPI_AMPLITUDE = 2, EPI_INTENSITY = 3 };
+struct Epilogue {
+    int mode = EPI_NONE;
+    const float* amp = nullptr;
+    float* inten = nullptr;
+};
 cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
-                           int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st);
+                           int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st,
+                           const Epilogue& ep = Epilogue());
 // column pass of a shared-source z-stack: one forward transform per column, `planes` outputs
 cudaError_t launch_col_stack(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
                              const float4* tw, const HParams& hp, cudaStream_t st);

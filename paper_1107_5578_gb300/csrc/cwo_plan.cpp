@@ -265,7 +265,7 @@ cwo_status check_plan_device(const cwo_plan* p) {
 }
 
 cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int batch,
-               const double* zs, void* stream, bool adjoint) {
+               const double* zs, void* stream, bool adjoint, const cwo::Epilogue& epi = cwo::Epilogue()) {
     if (!p) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
     if (batch < 1 || batch > 65535) return fail(CWO_ERR_INVALID_ARG, "batch must be in [1, 65535] (got %d)", batch);
     const long long field = (long long)p->nx * p->ny;
@@ -286,7 +286,13 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     const size_t fb = (size_t)field * sizeof(float2);
     const size_t in_bytes = stack ? fb : (size_t)((batch - 1) * (in_stride ? in_stride : field)) * sizeof(float2) + fb;
     if ((st = check_device_range(in, in_bytes, p->device, "input"))) return st;
-    if ((st = check_device_range(out, (size_t)batch * fb, p->device, "output"))) return st;
+    if (epi.mode != cwo::EPI_INTENSITY && (st = check_device_range(out, (size_t)batch * fb, p->device, "output"))) return st;
+    if (epi.mode != cwo::EPI_NONE) {
+        if (stack) return fail(CWO_ERR_INVALID_ARG, "output epilogues take one input per item (stride > 0)");
+        const size_t rb = (size_t)batch * field * sizeof(float);
+        if (epi.mode == cwo::EPI_AMPLITUDE && (st = check_device_range(epi.amp, rb, p->device, "amplitude"))) return st;
+        if (epi.mode == cwo::EPI_INTENSITY && (st = check_device_range(epi.inten, rb, p->device, "intensity"))) return st;
+    }
     const int need = stack ? batch + 1 : batch;
     if ((st = ensure_scratch(p, need))) return st;
 
@@ -412,7 +418,8 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         } else if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2))) {
             return cuda_fail(e, "column launch");
         }
-        if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 0, fout, field, p->ny, batch, scale, p->tw_x, p->status, s)) || (e = mark(3)))
+        if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 0, fout, field, p->ny, batch, scale, p->tw_x, p->status, s, epi)) ||
+            (e = mark(3)))
             return cuda_fail(e, "row inverse launch");
     }
     return CWO_OK;
@@ -640,6 +647,43 @@ cwo_status cwo_propagate_adjoint_batch(cwo_plan* plan, const void* in, long long
                                        void* out, int batch, const double* z_or_null, void* cuda_stream) {
     if (in_batch_stride == 0) return fail(CWO_ERR_INVALID_ARG, "the adjoint takes one input per item (stride > 0)");
     return run(plan, in, in_batch_stride, out, batch, z_or_null, cuda_stream, true);
+}
+
+cwo_status cwo_propagate_epilogue(cwo_plan* plan, const void* in_c64, void* out_c64, int batch, int adjoint,
+                                  int epilogue, const float* amplitude, float* intensity, void* cuda_stream) {
+    if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
+    if (epilogue < CWO_EPI_NONE || epilogue > CWO_EPI_INTENSITY) return fail(CWO_ERR_INVALID_ARG, "unknown epilogue %d", epilogue);
+    cwo::Epilogue ep;
+    ep.mode = epilogue;
+    ep.amp = amplitude;
+    ep.inten = intensity;
+    if (epilogue == CWO_EPI_AMPLITUDE && !amplitude) return fail(CWO_ERR_INVALID_ARG, "the amplitude epilogue needs an amplitude");
+    if (epilogue == CWO_EPI_INTENSITY && !intensity) return fail(CWO_ERR_INVALID_ARG, "the intensity epilogue needs an intensity buffer");
+    return run(plan, in_c64, (long long)plan->nx * plan->ny, out_c64, batch, nullptr, cuda_stream, adjoint != 0, ep);
+}
+
+cwo_status cwo_gs_run(cwo_plan* plan, const float* amplitude, void* field_c64, float* intensity, int batch,
+                      int iterations, void* cuda_stream) {
+    if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
+    if (plan->type != CWO_ANGULAR) return fail(CWO_ERR_UNSUPPORTED, "the GS iteration uses an angular-spectrum plan");
+    if (!amplitude || !field_c64) return fail(CWO_ERR_INVALID_ARG, "amplitude and field are required");
+    if (iterations < 0 || iterations > 1000000) return fail(CWO_ERR_INVALID_ARG, "iterations must be in [0, 1e6] (got %d)", iterations);
+    const long long f = (long long)plan->nx * plan->ny;
+    cwo::Epilogue ph, am, in;
+    ph.mode = cwo::EPI_PHASE;
+    am.mode = cwo::EPI_AMPLITUDE;
+    am.amp = amplitude;
+    in.mode = cwo::EPI_INTENSITY;
+    in.inten = intensity;
+    // hologram plane: propagate the object field by +z and keep the phase (the kinoform)
+    cwo_status st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, false, ph);
+    for (int i = 0; i < iterations && st == CWO_OK; ++i) {
+        // back to the object plane (conj(H) = H(-z)), amplitude constraint; forward, phase constraint
+        st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, true, am);
+        if (st == CWO_OK) st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, false, ph);
+    }
+    if (st == CWO_OK && intensity) st = run(plan, field_c64, f, nullptr, batch, nullptr, cuda_stream, true, in);
+    return st;
 }
 
 int cwo_launches_per_call(const cwo_plan* plan) { return plan ? 3 : 0; }

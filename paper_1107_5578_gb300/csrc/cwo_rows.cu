@@ -71,10 +71,33 @@ k_row_fwd(const float2* __restrict__ in, long long in_item_stride, const __grid_
     }
 }
 
-template <int P, int R>
+// Output epilogue of the inverse row pass, applied to the scaled value w of output element idx
+// (the GS constraints of Section "GS algorithm" fused into the pass that produces the field):
+//   EPI_NONE       out = w
+//   EPI_PHASE      out = w / |w|             (phase constraint; |w| = 0 gives 1)
+//   EPI_AMPLITUDE  out = amp[idx] w / |w|    (amplitude constraint)
+//   EPI_INTENSITY  inten[idx] = |w|^2        (reconstruction; out is not written)
+__device__ __forceinline__ float2 unit_phase(float2 w) {
+    const float m2 = w.x * w.x + w.y * w.y;
+    if (m2 > 0.f) {
+        const float r = rsqrtf(m2);
+        return make_float2(w.x * r, w.y * r);
+    }
+    return make_float2(1.f, 0.f);
+}
+
+template <int EPI>
+__device__ __forceinline__ void epilogue_store(float2* out, const Epilogue& ep, long long idx, float2 w) {
+    if constexpr (EPI == EPI_NONE) out[idx] = w;
+    else if constexpr (EPI == EPI_PHASE) out[idx] = unit_phase(w);
+    else if constexpr (EPI == EPI_AMPLITUDE) out[idx] = cscale(unit_phase(w), __ldg(ep.amp + idx));
+    else ep.inten[idx] = w.x * w.x + w.y * w.y;
+}
+
+template <int P, int R, int EPI>
 __global__ void __launch_bounds__(R * (P / 16))
 k_row_inv(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __restrict__ out,
-          long long out_item_stride, float scale, const float4* __restrict__ tw, int* status) {
+          long long out_item_stride, float scale, const float4* __restrict__ tw, int* status, const Epilogue ep) {
     constexpr int T = P / 16, N = P / 2, NT = R * T;
     constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
     extern __shared__ __align__(1024) float2 sm[];
@@ -95,9 +118,9 @@ k_row_inv(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __rest
     for (int e = 0; e < 16; ++e) v[e] = sm[e * NT + threadIdx.x];
     if (__syncthreads_or(!ok)) return;             // a copy did not land: the status word says so
     inv_from<P, R, PadLayout<P, R>, Geo<P>::NST - 1, 0, 0>(v, sm, r, t, TwTable<P>{tw, t});
-    float2* dst = out + item * out_item_stride + (long long)(y0 + r) * N;
+    const long long base = item * out_item_stride + (long long)(y0 + r) * N;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) dst[t + e * T] = cscale(v[e], scale);   // crop: first Nx outputs
+    for (int e = 0; e < 8; ++e) epilogue_store<EPI>(out, ep, base + t + e * T, cscale(v[e], scale));   // crop
 }
 
 // ------------------------------------------------------------------------------------------
@@ -212,18 +235,34 @@ static cudaError_t row_fwd_impl(const float2* in, long long in_item_stride, cons
     return cudaGetLastError();
 }
 
-template <int P>
-static cudaError_t row_inv_impl(const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
-                                int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st) {
+template <int P, int EPI>
+static cudaError_t row_inv_impl_e(const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
+                                  int ny, int items, float scale, const float4* tw, int* status, const Epilogue& ep,
+                                  cudaStream_t st) {
     constexpr int R = rows_inv<P>();
     constexpr int T = P / 16;
     const size_t smem = row_smem_words<P, R>() * sizeof(float2) + sizeof(uint64_t);   // tile + mbarrier
     if (ny % R) return cudaErrorInvalidValue;
-    cudaError_t e = ensure_smem(k_row_inv<P, R>, smem);
+    cudaError_t e = ensure_smem(k_row_inv<P, R, EPI>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / R, items);
-    k_row_inv<P, R><<<grid, R * T, smem, st>>>(*wmap, item_off, out, out_item_stride, scale, tw, status);
+    k_row_inv<P, R, EPI><<<grid, R * T, smem, st>>>(*wmap, item_off, out, out_item_stride, scale, tw, status, ep);
     return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t row_inv_impl(const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
+                                int ny, int items, float scale, const float4* tw, int* status, const Epilogue& ep,
+                                cudaStream_t st) {
+    switch (ep.mode) {
+        case EPI_NONE: return row_inv_impl_e<P, EPI_NONE>(wmap, item_off, out, out_item_stride, ny, items, scale, tw, status, ep, st);
+        case EPI_PHASE: return row_inv_impl_e<P, EPI_PHASE>(wmap, item_off, out, out_item_stride, ny, items, scale, tw, status, ep, st);
+        case EPI_AMPLITUDE:
+            return row_inv_impl_e<P, EPI_AMPLITUDE>(wmap, item_off, out, out_item_stride, ny, items, scale, tw, status, ep, st);
+        case EPI_INTENSITY:
+            return row_inv_impl_e<P, EPI_INTENSITY>(wmap, item_off, out, out_item_stride, ny, items, scale, tw, status, ep, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 #define CWO_P_CASES(X) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
@@ -281,9 +320,10 @@ cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, c
 }
 
 cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
-                           int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st) {
+                           int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st,
+                           const Epilogue& ep) {
     switch (px) {
-#define CASE(P) case P: return row_inv_impl<P>(wmap, item_off, out, out_item_stride, ny, items, scale, tw, status, st);
+#define CASE(P) case P: return row_inv_impl<P>(wmap, item_off, out, out_item_stride, ny, items, scale, tw, status, ep, st);
         CWO_P_CASES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;

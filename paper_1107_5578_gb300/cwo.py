@@ -22,6 +22,7 @@ SHIFTED_ANGULAR = 4
 # flags
 FLAG_PHASE_FP32 = 0x1
 FLAG_PHASE_FP64 = 0x2
+EPI_NONE, EPI_PHASE, EPI_AMPLITUDE, EPI_INTENSITY = 0, 1, 2, 3
 FLAG_LITERAL_SCALE = 0x4
 # status
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = range(6)
@@ -70,6 +71,8 @@ def lib() -> ctypes.CDLL:
                 "cwo_propagate_adjoint_batch": ([vp, vp, ll, vp, i, dpp, vp], i),
                 "cwo_propagate_items": ([vp, vp, ll, vp, i, ctypes.POINTER(Item), vp], i),
                 "cwo_launches_per_call": ([vp], i),
+                "cwo_propagate_epilogue": ([vp, vp, vp, i, i, i, vp, vp, vp], i),
+                "cwo_gs_run": ([vp, vp, vp, vp, i, i, vp], i),
                 "cwo_plan_check": ([vp], i),
                 "cwo_plan_set_timing_events": ([vp, ctypes.POINTER(ctypes.c_void_p)], i),
                 "cwo_last_error": ([], ctypes.c_char_p),
@@ -125,6 +128,18 @@ def _check_field(t, nx: int, ny: int, name: str, batch: int | None = None):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected [..., {ny}, {nx}]")
     if batch is not None and t.numel() != batch * nx * ny:
         raise ValueError(f"{name} holds {t.numel() // (nx * ny)} fields, expected {batch}")
+
+
+def _check_real(t, nx: int, ny: int, name: str, batch: int):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32 (got {t.dtype})")
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if tuple(t.shape[-2:]) != (ny, nx) or t.numel() != batch * nx * ny:
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {batch} x [{ny}, {nx}]")
 
 
 class Plan:
@@ -236,6 +251,46 @@ class Plan:
                                         ctypes.c_void_p(out.data_ptr()), b, arr, _stream_handle(stream)),
               "cwo_propagate_items")
         return out
+
+    def propagate_epilogue(self, x, epilogue, amplitude=None, out=None, adjoint=False, stream=None):
+        """Batch [B][Ny][Nx] (or one field) propagated (adjoint: by conj(H)) with an output
+        epilogue: EPI_PHASE (unit amplitude), EPI_AMPLITUDE (amplitude * phase; ``amplitude`` a
+        float32 tensor shaped like x) or EPI_INTENSITY (returns |u|^2 as float32)."""
+        import torch
+        b = x.shape[0] if x.dim() == 3 else 1
+        _check_field(x, self.nx, self.ny, "input", b)
+        inten = None
+        if epilogue == EPI_INTENSITY:
+            inten = torch.empty(x.shape, dtype=torch.float32, device=x.device) if out is None else out
+            _check_real(inten, self.nx, self.ny, "intensity", b)
+            optr = None
+        else:
+            out = self._out(x, x.shape[:-2]) if out is None else out
+            _check_field(out, self.nx, self.ny, "output", b)
+            optr = out.data_ptr()
+        aptr = None
+        if epilogue == EPI_AMPLITUDE:
+            _check_real(amplitude, self.nx, self.ny, "amplitude", b)
+            aptr = amplitude.data_ptr()
+        check(lib().cwo_propagate_epilogue(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(optr), b,
+                                           int(bool(adjoint)), int(epilogue), ctypes.c_void_p(aptr),
+                                           ctypes.c_void_p(inten.data_ptr() if inten is not None else None),
+                                           _stream_handle(stream)), "cwo_propagate_epilogue")
+        return inten if epilogue == EPI_INTENSITY else out
+
+    def gs_run(self, amplitude, field, iterations, intensity=True, stream=None):
+        """Gerchberg-Saxton kinoform iteration in place on ``field`` ([B][Ny][Nx] or one field;
+        in: amplitude * initial phase, out: the kinoform).  Returns the reconstructed intensity
+        (float32, like ``amplitude``) or None."""
+        import torch
+        b = field.shape[0] if field.dim() == 3 else 1
+        _check_field(field, self.nx, self.ny, "field", b)
+        _check_real(amplitude, self.nx, self.ny, "amplitude", b)
+        inten = torch.empty(amplitude.shape, dtype=torch.float32, device=field.device) if intensity else None
+        check(lib().cwo_gs_run(self.handle, ctypes.c_void_p(amplitude.data_ptr()), ctypes.c_void_p(field.data_ptr()),
+                               ctypes.c_void_p(inten.data_ptr() if inten is not None else None), b, int(iterations),
+                               _stream_handle(stream)), "cwo_gs_run")
+        return inten
 
     def propagate_stack(self, x, zs, out=None, stream=None):
         """One source [Ny][Nx] propagated to len(zs) planes in one batched call (shared spectrum)."""
