@@ -32,6 +32,7 @@ namespace cwo {
 // span at least 16 contiguous bytes, hence >= 2 rows.
 template <int P> constexpr int rows_fwd() { return P >= 8192 ? 2 : (P >= 4096 ? 4 : (P >= 256 ? 4 : 8)); }
 template <int P> constexpr int rows_inv() { return P >= 4096 ? 2 : (P >= 256 ? 4 : 8); }
+constexpr bool kRowInvPersistent = true;   // measured: 25.4 -> 23.0 us per 2048^2 field
 
 template <int P, int R>
 __host__ __device__ constexpr size_t row_smem_words() {
@@ -173,11 +174,20 @@ k_row_fwd_p(const float2* __restrict__ in, long long in_item_stride, const __gri
         for (int e = 0; e < 8; ++e) v[e] = stage[r * SST + t + e * T];   // DIF stage-0 positions t + e P/16
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);      // zero padding, never loaded
-        if (threadIdx.x == 0) tma_store_wait_read();                     // previous tile read out
         fence_proxy_async_smem();   // these reads of the staging buffer precede the next bulk copy into it
         if (__syncthreads_or(!ok)) break;                                // a copy did not land
         if (threadIdx.x == 0 && g + (int)gridDim.x < total_groups) issue(g + gridDim.x);
-        fwd_from<P, R, PadLayout<P, R>, 0, 8, 0>(v, sm, r, t, TwTable<P>{tw, t});
+        // first stage in registers while the previous tile's stores drain; the exchange region
+        // (which the tile aliases) is rewritten only after the drain
+        const TwTable<P> twt{tw, t};
+        stage_butterflies<P, 0, false, 8>(v);
+        if constexpr (Geo<P>::NST > 1) twt.template apply<0, false>(v);
+        if (threadIdx.x == 0) tma_store_wait_read();
+        __syncthreads();
+        if constexpr (Geo<P>::NST > 1) {
+            exchange<P, R, PadLayout<P, R>, 0, 1, 0, 0>(sm, r, t, v);
+            fwd_from<P, R, PadLayout<P, R>, 1, 8, 0>(v, sm, r, t, twt);
+        }
 #pragma unroll
         for (int e = 0; e < 16; ++e) sm[e * NT + threadIdx.x] = v[e];
         fence_proxy_async_smem();
@@ -190,6 +200,64 @@ k_row_fwd_p(const float2* __restrict__ in, long long in_item_stride, const __gri
         }
     }
     if (threadIdx.x == 0) tma_store_wait_read();
+}
+
+// Inverse, persistent: R rows per group, one tile buffer.  The tile of the NEXT group is
+// requested as soon as the last exchange of the current group has been read back, so its load
+// overlaps the last stage, the crop and the stores of the current group.
+template <int P, int C, class Lay, int S, int PING, int XOFF, class Tw>
+__device__ __forceinline__ void inv_to_stage0(float2 (&v)[16], float2* __restrict__ sm, int c, int t, const Tw& tw) {
+    using G = Geo<P>;
+    if constexpr (S < G::NST - 1) tw.template apply<S, true>(v);
+    stage_butterflies<P, S, true, 16>(v);
+    exchange<P, C, Lay, S, S - 1, PING, XOFF + (G::NST - 1 - S)>(sm, c, t, v);
+    if constexpr (S > 1) inv_to_stage0<P, C, Lay, S - 1, PING, XOFF>(v, sm, c, t, tw);
+}
+
+template <int P, int R> constexpr int row_inv_p_min_blocks() { return R * (P / 16) >= 1024 ? 1 : 1024 / (R * (P / 16)); }
+
+template <int P, int R, int EPI>
+__global__ void __launch_bounds__(R * (P / 16), row_inv_p_min_blocks<P, R>())
+k_row_inv_p(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __restrict__ out,
+            long long out_item_stride, int groups_per_item, int total_groups, float scale,
+            const float4* __restrict__ tw, int* status, const Epilogue ep) {
+    constexpr int T = P / 16, N = P / 2, NT = R * T;
+    constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
+    static_assert(Geo<P>::NST >= 2, "at least two stages");
+    extern __shared__ __align__(1024) float2 sm[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + row_smem_words<P, R>());   // after the tile
+    const int r = threadIdx.x % R, t = threadIdx.x / R;
+    auto issue = [&](int g) {   // thread 0: the R-row tile of group g
+        const int item = g / groups_per_item, y0 = (g % groups_per_item) * R;
+        mbar_arrive_expect_tx(mbar, (unsigned)(R * P * sizeof(float2)));
+#pragma unroll 1
+        for (int b = 0; b < P / BOX; ++b) tma_load_3d(sm + b * BOX * R, &wmap, mbar, y0, b * BOX, item + item_off);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        if ((int)blockIdx.x < total_groups) issue(blockIdx.x);
+    }
+    __syncthreads();
+    const TwTable<P> twt{tw, t};
+    unsigned parity = 0;
+#pragma unroll 1
+    for (int g = blockIdx.x; g < total_groups; g += gridDim.x, parity ^= 1u) {
+        const bool ok = mbar_wait_bounded(mbar, parity, status);
+        float2 v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = sm[e * NT + threadIdx.x];
+        if (__syncthreads_or(!ok)) break;          // a copy did not land: the status word says so
+        inv_to_stage0<P, R, PadLayout<P, R>, Geo<P>::NST - 1, 0, 0>(v, sm, r, t, twt);
+        fence_proxy_async_smem();                  // the exchange reads precede the next tile load
+        __syncthreads();
+        if (threadIdx.x == 0 && g + (int)gridDim.x < total_groups) issue(g + gridDim.x);
+        twt.template apply<0, true>(v);
+        stage_butterflies<P, 0, true, 16>(v);
+        const int item = g / groups_per_item, y0 = (g % groups_per_item) * R;
+        const long long base = item * out_item_stride + (long long)(y0 + r) * N;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) epilogue_store<EPI>(out, ep, base + t + e * T, cscale(v[e], scale));   // crop
+    }
 }
 
 template <typename K>
@@ -243,6 +311,17 @@ static cudaError_t row_inv_impl_e(const CUtensorMap* wmap, int item_off, float2*
     constexpr int T = P / 16;
     const size_t smem = row_smem_words<P, R>() * sizeof(float2) + sizeof(uint64_t);   // tile + mbarrier
     if (ny % R) return cudaErrorInvalidValue;
+    if constexpr (kRowInvPersistent && P >= 512) {
+        cudaError_t e = ensure_smem(k_row_inv_p<P, R, EPI>, smem);
+        if (e != cudaSuccess) return e;
+        const int groups = (ny / R) * items;
+        const int grid = persistent_grid(k_row_inv_p<P, R, EPI>, R * T, smem, groups);
+        if (grid > 0) {
+            k_row_inv_p<P, R, EPI><<<grid, R * T, smem, st>>>(*wmap, item_off, out, out_item_stride, ny / R, groups,
+                                                              scale, tw, status, ep);
+            return cudaGetLastError();
+        }
+    }
     cudaError_t e = ensure_smem(k_row_inv<P, R, EPI>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / R, items);
