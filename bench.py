@@ -36,6 +36,17 @@ BYTES_PER_PROP = 80 * N * N          # 3 passes: 8N^2 + 16N^2 | 16N^2 + 16N^2 | 
 COL_BYTES_PER_PROP = 32 * N * N      # column pass: read + write the Ny x Px intermediate
 
 
+# DRAM bytes (read + write) per launch of each pass at batch 16, from one ncu capture of this
+# build's kernels (profiles/asm_2048_batch16_launches.md); scaled by the batch (traffic grows in
+# proportion to the fields processed)
+NCU_TRAFFIC_B16 = {"col_fwd_h_inv": 2083.8e6}
+
+
+def traffic_bytes(kernel, batch):
+    t = NCU_TRAFFIC_B16.get(kernel)
+    return None if t is None else round(t * batch / 16)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -364,7 +375,7 @@ def main():
                    "parallelism": f"independent items per rank x{world}"},
         "hbm_gbs_path": round(path_gbs, 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                     "frac": round(achieved / hbm_peak, 4), "traffic": traffic_bytes(names[dom], B),
                      "kernel": names[dom], "peak_kind": peak_kind},
         "roofline_path": {"achieved": round(path_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                           "frac": round(path_gbs / hbm_peak, 4), "bytes_per_prop": BYTES_PER_PROP},
