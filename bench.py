@@ -36,8 +36,8 @@ BYTES_PER_PROP = 80 * N * N          # 3 passes: 8N^2 + 16N^2 | 16N^2 + 16N^2 | 
 COL_BYTES_PER_PROP = 32 * N * N      # column pass: read + write the Ny x Px intermediate
 
 
-# DRAM bytes (read + write) per launch of each pass at batch 16, from one ncu capture of this
-# build's kernels (profiles/asm_2048_batch16_launches.md); scaled by the batch (traffic grows in
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the column pass at
+# batch 16, from one ncu capture of the current kernel; scaled by the batch (traffic grows in
 # proportion to the fields processed)
 NCU_TRAFFIC_B16 = {"col_fwd_h_inv": 2083.8e6}
 
