@@ -19,6 +19,11 @@ Pins (each checked by the ``-m "not gpu"`` tests, none of them by re-calling thi
                           constraint, unit-amplitude kinoform, and on the circular (unitary)
                           grid the error-reduction property: the object-plane amplitude error
                           never increases from one iteration to the next
+  * ``propagate_shifted`` -- no shift and no window = ``propagate``; on the circular grid a shift
+                          of whole pixels is an exact translation; the window removes the
+                          spectrum outside it
+  * ``band_limit``     -- the limit is where the transfer phase's slope reaches the Nyquist rate
+                          of the padded frequency grid (finite differences of the phase)
 """
 from __future__ import annotations
 
@@ -224,3 +229,70 @@ def gs_amplitude_errors(amplitude, field0, dx: float, dy: float, lam: float, z: 
             break
         u = phase_only(propagate(a1 * phase_only(back), dx, dy, lam, z, ANGULAR, flags))
     return np.array(errs)
+
+
+def signed_freqs(p: int, pitch: float) -> np.ndarray:
+    """Frequencies of the bins of a length-p axis: kt / (p pitch), kt = k (k < p/2) else k - p."""
+    k = np.arange(p)
+    return np.where(k < p // 2, k, k - p) / (p * pitch)
+
+
+def rect(x) -> np.ndarray:
+    """Rect(x) = 1 for |x| <= 1/2, else 0 (the window edge counts as inside)."""
+    return (np.abs(np.asarray(x, dtype=np.float64)) <= 0.5).astype(np.float64)
+
+
+def shifted_asm_transfer(px: int, py: int, dx: float, dy: float, lam: float, z: float,
+                         ox: float = 0.0, oy: float = 0.0, cx: float = 0.0, wx: float = 0.0,
+                         cy: float = 0.0, wy: float = 0.0) -> np.ndarray:
+    """Shifted angular spectrum transfer function (Section "Shifted angular spectrum method",
+    Eqs. shift_ang1 and shift_ang2 with the imaginary unit restored): H_A of Eq. ang2 times
+    exp(i 2 pi (ox fx + oy fy)) times Rect((fx - cx) / wx) Rect((fy - cy) / wy); a width <= 0
+    means no window on that axis.  Frequencies on the padded grid (signed_freqs)."""
+    H = asm_transfer(px, py, dx, dy, lam, z)
+    fx = signed_freqs(px, dx)[None, :]
+    fy = signed_freqs(py, dy)[:, None]
+    H = H * np.exp(2j * np.pi * (ox * fx + oy * fy))
+    if wx > 0:
+        H = H * rect((fx - cx) / wx)
+    if wy > 0:
+        H = H * rect((fy - cy) / wy)
+    return H
+
+
+def propagate_shifted(u1, dx: float, dy: float, lam: float, z: float, ox: float = 0.0, oy: float = 0.0,
+                      cx: float = 0.0, wx: float = 0.0, cy: float = 0.0, wy: float = 0.0,
+                      flags: int = 0) -> np.ndarray:
+    """Shifted ASM propagation: pad to 2N (NO_PAD: circular on N), FFT2, multiply by the shifted
+    and windowed transfer function, inverse FFT2, crop (FULL_OUTPUT: keep the padded grid).
+    ADJOINT multiplies by conj(H)."""
+    u1 = _c128(u1)
+    ny, nx = u1.shape
+    if flags & NO_PAD:
+        py, px = ny, nx
+        g = u1.copy()
+    else:
+        py, px = 2 * ny, 2 * nx
+        g = np.zeros((py, px), dtype=np.complex128)
+        g[:ny, :nx] = u1
+    H = shifted_asm_transfer(px, py, dx, dy, lam, z, ox, oy, cx, wx, cy, wy)
+    if flags & ADJOINT:
+        H = np.conj(H)
+    G = fft2(g, -1) * H
+    out = fft2(G, +1) / (px * py)
+    if flags & FULL_OUTPUT or flags & NO_PAD:
+        return out
+    return out[:ny, :nx]
+
+
+def band_limit(nx: int, ny: int, dx: float, dy: float, lam: float, z: float):
+    """On-axis band limit of the angular spectrum method (Matsushima and Shimobaba, "Band-limited
+    angular spectrum method", Opt. Express 17, 19662 (2009)): on the padded grid with frequency
+    pitch df = 1/(P pitch) the transfer function's phase is sampled without aliasing for
+    |f| <= 1 / (lam sqrt((2 df z)^2 + 1)).  Returns (wx, wy): the full widths of the Rect
+    windows centred on zero frequency."""
+    dfx = 1.0 / (2 * nx * dx)
+    dfy = 1.0 / (2 * ny * dy)
+    ux = 1.0 / (lam * np.sqrt((2 * dfx * z) ** 2 + 1.0))
+    uy = 1.0 / (lam * np.sqrt((2 * dfy * z) ** 2 + 1.0))
+    return 2.0 * ux, 2.0 * uy

@@ -318,3 +318,52 @@ def test_gs_planted_amplitude_error_is_caught():
     errs_ok = oracle.gs_amplitude_errors(amp, f0, 8e-6, 8e-6, 532e-9, 0.0, 1)
     errs_bad = oracle.gs_amplitude_errors(wrong_amp, f0, 8e-6, 8e-6, 532e-9, 0.0, 1)
     assert np.all(errs_ok > 0) and not np.allclose(errs_ok, errs_bad)
+
+
+# ---------------------------------------------------------------------------------------------
+# Shifted / band-limited angular spectrum (Section "Shifted angular spectrum method")
+# ---------------------------------------------------------------------------------------------
+def test_shifted_asm_without_shift_or_window_is_asm():
+    u = synth.random_field(32, seed=21, ny=16)
+    got = oracle.propagate_shifted(u, 6e-6, 8e-6, 532e-9, 0.01)
+    want = oracle.propagate(u, 6e-6, 8e-6, 532e-9, 0.01)
+    assert np.max(np.abs(got - want)) < 1e-12
+
+
+@pytest.mark.parametrize("mx,my", [(3, 0), (-5, 2), (7, -4)])
+def test_shifted_asm_is_a_translation_on_the_circular_grid(mx, my):
+    # exp(i 2 pi ox fx) with ox = mx dx on the unpadded N-grid is exactly a circular shift of the
+    # ASM result by -mx pixels: u_SA(x) = u_A(x + ox)
+    n, dx = 32, 8e-6
+    u = synth.random_field(n, seed=22)
+    shifted = oracle.propagate_shifted(u, dx, dx, 633e-9, 0.005, ox=mx * dx, oy=my * dx, flags=oracle.NO_PAD)
+    plain = oracle.propagate_shifted(u, dx, dx, 633e-9, 0.005, flags=oracle.NO_PAD)
+    assert np.max(np.abs(shifted - np.roll(plain, (-my, -mx), axis=(0, 1)))) < 1e-12
+
+
+def test_window_removes_the_spectrum_outside():
+    n, dx = 32, 8e-6
+    u = synth.random_field(n, seed=23)
+    wx, wy = 1.0 / (4 * dx), 1.0 / (3 * dx)
+    cx, cy = 1.0 / (16 * dx), -1.0 / (20 * dx)
+    full = oracle.propagate_shifted(u, dx, dx, 633e-9, 0.02, cx=cx, wx=wx, cy=cy, wy=wy, flags=oracle.FULL_OUTPUT)
+    spec = np.fft.fft2(full)
+    fx = np.fft.fftfreq(2 * n, dx)[None, :]
+    fy = np.fft.fftfreq(2 * n, dx)[:, None]
+    outside = (np.abs(fx - cx) > wx / 2) | (np.abs(fy - cy) > wy / 2)
+    assert outside.sum() > 0
+    assert np.max(np.abs(spec[outside])) < 1e-9 * np.max(np.abs(spec))
+
+
+@pytest.mark.parametrize("n,dx,lam,z", [(256, 10e-6, 633e-9, 0.5), (512, 4e-6, 532e-9, 0.2), (128, 8e-6, 450e-9, 2.0)])
+def test_band_limit_is_the_nyquist_rate_of_the_transfer_phase(n, dx, lam, z):
+    # at f = u_limit the local "frequency" of the transfer-function phase in the frequency domain,
+    # |d(z sqrt(1/lam^2 - f^2)) / df| = z f / sqrt(1/lam^2 - f^2), equals the Nyquist limit
+    # 1 / (2 df) of the padded grid's frequency sampling df = 1 / (2 n dx)
+    wx, _ = oracle.band_limit(n, n, dx, dx, lam, z)
+    u = wx / 2
+    df = 1.0 / (2 * n * dx)
+    h = 1e-6 * u
+    psi = lambda f: z * np.sqrt(1.0 / lam ** 2 - f ** 2)
+    slope = abs(psi(u + h) - psi(u - h)) / (2 * h)
+    assert abs(slope * 2 * df - 1.0) < 1e-6
