@@ -70,7 +70,8 @@ typedef enum {
     CWO_FRESNEL_CONV = 1,     /* Fresnel diffraction, convolution form (Eq. fre_conv_fft) */
     CWO_FRESNEL_FOURIER = 2,  /* Fourier form (Eq. fre_fourier3): not provided, UNSUPPORTED */
     CWO_SHIFTED_FRESNEL = 3,  /* shifted Fresnel: not provided, UNSUPPORTED               */
-    CWO_SHIFTED_ANGULAR = 4   /* shifted angular spectrum: not provided, UNSUPPORTED      */
+    CWO_SHIFTED_ANGULAR = 4   /* shifted angular spectrum (Eqs. shift_ang1, shift_ang2): plans come
+                                 from cwo_plan_create_shifted                             */
 } cwo_type;
 
 typedef enum {
@@ -98,6 +99,33 @@ typedef struct cwo_plan cwo_plan;
  */
 cwo_status cwo_plan_create(int nx, int ny, double dx, double dy, double lambda, double z,
                            cwo_type type, unsigned flags, cwo_plan** out);
+
+/* Shifted angular spectrum parameters (Section "Shifted angular spectrum method",
+ * Eqs. shift_ang1 and shift_ang2, the imaginary unit of the shift phase restored):
+ *   H_SA = H_A(fx, fy) exp(i 2 pi (ox fx + oy fy)) Rect((fx - cx) / wx) Rect((fy - cy) / wy)
+ * ox, oy: shift of the destination window (metres); cx, wx, cy, wy: centre and full width of the
+ * band-limit windows (1/metre, on the padded grid's frequencies kt / (2N pitch)); a width <= 0
+ * means no window on that axis; Rect(x) = 1 for |x| <= 1/2.  The paper leaves the choice of the
+ * windows to the shifted-ASM literature; cwo_band_limit gives the on-axis band limit. */
+typedef struct {
+    double ox, oy;
+    double cx, wx;
+    double cy, wy;
+} cwo_shift;
+
+/* A CWO_SHIFTED_ANGULAR plan: like cwo_plan_create(..., CWO_ANGULAR, ...) with the shift phase
+ * and windows folded into the per-axis FP64 tables.  flags: 0 or CWO_FLAG_PHASE_FP64
+ * (CWO_FLAG_PHASE_FP32: CWO_ERR_UNSUPPORTED).  Per-item distances (z_or_null) are not provided
+ * for these plans (CWO_ERR_UNSUPPORTED); batches, z-stacks of the plan's z, the adjoint and the
+ * epilogues are.  CWO_ERR_INVALID_ARG for non-finite parameters or a window that holds no bin. */
+cwo_status cwo_plan_create_shifted(int nx, int ny, double dx, double dy, double lambda, double z,
+                                   const cwo_shift* shift, unsigned flags, cwo_plan** out);
+
+/* The on-axis band-limited angular spectrum method (Matsushima and Shimobaba, Opt. Express 17,
+ * 19662 (2009)): fills *out with no shift and windows centred on zero of full width 2 u, where
+ * u = 1 / (lambda sqrt((2 df z)^2 + 1)), df = 1 / (2N pitch), the frequency beyond which the
+ * transfer function's phase is undersampled on the padded grid.  Host only. */
+cwo_status cwo_band_limit(int nx, int ny, double dx, double dy, double lambda, double z, cwo_shift* out);
 
 /* Release a plan (NULL is accepted).  The caller must make sure no work using it is pending. */
 cwo_status cwo_plan_destroy(cwo_plan* plan);

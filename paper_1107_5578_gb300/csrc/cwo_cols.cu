@@ -87,6 +87,16 @@ __device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int co
         }
     } else {
         const int kbx = __ldg(hp.kbx + col);
+        if (hp.asym) {   // shifted ASM, per-element FP64: window and shift phase
+            const bool inx = kbx >= hp.wxlo && kbx <= hp.wxhi;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int kby = __ldg(hp.kby + e * T + t);
+                const bool in = inx && kby >= hp.wylo && kby <= hp.wyhi;
+                mul(e, in ? asm_h_fp64_shifted(kbx, kby, Kd, sx, sy, hp.shx, hp.shy) : make_float2(0.f, 0.f));
+            }
+            return;
+        }
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
             const int kby = __ldg(hp.kby + e * T + t);
@@ -215,7 +225,13 @@ static cudaError_t col_impl_t(const float2* win, long long win_item_stride, floa
                               const HParams& hp, cudaStream_t st) {
     constexpr int T = P / 16;
     cudaError_t e;
-    if constexpr (col_paired<P>()) {
+    if (hp.asym) {   // H(kx) != H(-kx): one column per transform
+        constexpr int C = cols_per_block<P>();
+        if (px % C != 0) return cudaErrorInvalidValue;
+        const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
+        if ((e = set_smem(k_col<P, C, MIXED>, smem))) return e;
+        k_col<P, C, MIXED><<<dim3(px / C, items), C * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
+    } else if constexpr (col_paired<P>()) {
         constexpr int CP = cols_per_block<P>();
         const size_t smem = (size_t)PadLayout<P, 2 * CP>::WORDS * sizeof(float2);
         if ((e = set_smem(k_colp<P, CP, MIXED>, smem))) return e;

@@ -71,4 +71,21 @@ CWO_HD float2 asm_h_fp64(int kbx, int kby, double K, double sx, double sy) {
     return make_float2(cs, sn);
 }
 
+// The same with the shifted ASM's extra phase shx kbx + shy kby cycles (Eq. shift_ang2), in FP64
+// before the reduction.
+CWO_HD float2 asm_h_fp64_shifted(int kbx, int kby, double K, double sx, double sy, double shx, double shy) {
+    const double s = sx * (double)kbx * (double)kbx + sy * (double)kby * (double)kby;
+    if (s > 1.0) return make_float2(0.f, 0.f);
+    double psi = K * sqrt(1.0 - s) + shx * (double)kbx + shy * (double)kby;
+    psi -= rint(psi);
+    float sn, cs;
+#ifdef __CUDA_ARCH__
+    sincospif(2.0f * (float)psi, &sn, &cs);
+#else
+    sn = (float)sin(2.0 * 3.14159265358979323846 * psi);
+    cs = (float)cos(2.0 * 3.14159265358979323846 * psi);
+#endif
+    return make_float2(cs, sn);
+}
+
 }  // namespace cwo

@@ -53,6 +53,11 @@ struct HParams {
     // mixed batch: per-item modes and scalars (nullptr: the launch-wide fields above apply);
     // the tables are then ax / ay (float4) with x_item_stride / y_item_stride for every mode
     const ItemParams* items;
+    // shifted ASM: tables not symmetric in kx (single-column kernel); for the per-element FP64
+    // evaluation the shift in cycles per signed bin and the signed-bin window [lo, hi]
+    int asym;
+    double shx, shy;
+    int wxlo, wxhi, wylo, wyhi;
 };
 
 // launchers (return cudaGetLastError() after the launch)

@@ -160,6 +160,9 @@ struct cwo_plan {
     CUtensorMap wmap_f;        // TMA maps of the scratch intermediate [scap][px][ny] for the
     CUtensorMap wmap_i;        // forward and inverse row passes (different box heights)
     int* status = nullptr;     // device status word: bounded waits that expired (cwo_plan_check)
+    // shifted angular spectrum (CWO_SHIFTED_ANGULAR): shift and Rect windows (Eq. shift_ang1)
+    bool shifted = false;
+    cwo_shift shift{};
 };
 
 namespace {
@@ -205,6 +208,12 @@ cwo_status check_params(int nx, int ny, double dx, double dy, double lambda, dou
 
 // host tables of one parameter set
 void host_h_tables(const cwo_plan* p, double z, float4* ax, float4* ay, float2* hx, float2* hy, float* kf) {
+    if (p->shifted) {
+        asm_axis_table_shifted(AxisGeo(p->px), p->dx, p->lambda, z, true, p->shift.ox, p->shift.cx, p->shift.wx, ax);
+        asm_axis_table_shifted(AxisGeo(p->py), p->dy, p->lambda, z, false, p->shift.oy, p->shift.cy, p->shift.wy, ay);
+        if (kf) *kf = (float)(z / p->lambda);
+        return;
+    }
     make_h_tables(p->px, p->py, p->dx, p->dy, p->lambda, z, p->type == CWO_FRESNEL_CONV,
                   (p->flags & CWO_FLAG_LITERAL_SCALE) != 0, ax, ay, hx, hy, kf);
 }
@@ -273,6 +282,8 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     if (in_stride != 0 && in_stride < field) return fail(CWO_ERR_INVALID_ARG, "input batch stride %lld smaller than one field (%lld)", in_stride, field);
     if (adjoint && in_stride == 0 && batch > 1) return fail(CWO_ERR_INVALID_ARG, "the adjoint takes one input per item (stride > 0)");
     const bool stack = in_stride == 0 && batch > 1;
+    if (zs && p->shifted)
+        return fail(CWO_ERR_UNSUPPORTED, "per-item distances are not provided for a shifted angular-spectrum plan");
     if (zs) {
         if (p->flags & (CWO_FLAG_PHASE_FP32 | CWO_FLAG_PHASE_FP64))
             return fail(CWO_ERR_UNSUPPORTED, "per-item distances are not provided with the phase-precision study flags");
@@ -311,6 +322,13 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     hp.k = 2.0 * kPi / p->lambda;
     hp.dfx = 1.0 / ((double)p->px * p->dx);
     hp.dfy = 1.0 / ((double)p->py * p->dy);
+    if (p->shifted) {
+        hp.asym = 1;
+        hp.shx = p->shift.ox * hp.dfx;
+        hp.shy = p->shift.oy * hp.dfy;
+        window_bins(AxisGeo(p->px), p->dx, p->shift.cx, p->shift.wx, &hp.wxlo, &hp.wxhi);
+        window_bins(AxisGeo(p->py), p->dy, p->shift.cy, p->shift.wy, &hp.wylo, &hp.wyhi);
+    }
     if (p->type == CWO_FRESNEL_CONV) hp.mode = cwo::HMODE_FRESNEL;
     else if (p->flags & CWO_FLAG_PHASE_FP32) hp.mode = cwo::HMODE_ASM_FP32;
     else if (p->flags & CWO_FLAG_PHASE_FP64) hp.mode = cwo::HMODE_ASM_FP64;
@@ -549,30 +567,18 @@ cwo_status run_items(cwo_plan* p, const void* in, long long in_stride, void* out
 // ------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------
-extern "C" {
-
-const char* cwo_last_error(void) { return g_err.c_str(); }
-
-int cwo_version(void) { return 1 * 10000 + 0 * 100 + 0; }
-
-cwo_status cwo_plan_device_bytes(int nx, int ny, int batch, size_t* bytes) {
-    if (!bytes) return fail(CWO_ERR_INVALID_ARG, "bytes is NULL");
-    if (!pow2_side(nx) || !pow2_side(ny)) return fail(CWO_ERR_INVALID_ARG, "Nx=%d, Ny=%d out of range", nx, ny);
-    if (batch < 1) return fail(CWO_ERR_INVALID_ARG, "batch must be >= 1");
-    *bytes = tables_bytes(nx, ny) + (size_t)batch * ny * (2 * (size_t)nx) * sizeof(float2);
-    return CWO_OK;
-}
-
-cwo_status cwo_plan_create(int nx, int ny, double dx, double dy, double lambda, double z,
-                           cwo_type type, unsigned flags, cwo_plan** out) {
-    if (!out) return fail(CWO_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    cwo_status st = check_params(nx, ny, dx, dy, lambda, z, (int)type, flags);
-    if (st) return st;
+namespace {
+cwo_status create_impl(int nx, int ny, double dx, double dy, double lambda, double z, cwo_type type, unsigned flags,
+                       const cwo_shift* shift, cwo_plan** out) {
+    cwo_status st;
     cwo_plan* p = new (std::nothrow) cwo_plan();
     if (!p) return fail(CWO_ERR_OOM, "host allocation failed");
     p->nx = nx; p->ny = ny; p->px = 2 * nx; p->py = 2 * ny;
     p->dx = dx; p->dy = dy; p->lambda = lambda; p->z = z; p->type = type; p->flags = flags;
+    if (shift) {
+        p->shifted = true;
+        p->shift = *shift;
+    }
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaGetDevice"); }
 
@@ -590,7 +596,7 @@ cwo_status cwo_plan_create(int nx, int ny, double dx, double dy, double lambda, 
     if ((st = dev_alloc(&p->pairs_x, prs.size(), "x pairs")) || (st = upload(p->pairs_x, prs, "x pair upload"))) { free_plan(p); return st; }
     if ((st = dev_alloc(&p->kb_x, kbx.size(), "x bins")) || (st = upload(p->kb_x, kbx, "x bin upload")) ||
         (st = dev_alloc(&p->kb_y, kby.size(), "y bins")) || (st = upload(p->kb_y, kby, "y bin upload"))) { free_plan(p); return st; }
-    if (type == CWO_ANGULAR) {
+    if (type == CWO_ANGULAR || type == CWO_SHIFTED_ANGULAR) {
         std::vector<float4> ax(p->px), ay(p->py);
         std::vector<float> kf(1);
         host_h_tables(p, z, ax.data(), ay.data(), nullptr, nullptr, kf.data());
@@ -607,6 +613,62 @@ cwo_status cwo_plan_create(int nx, int ny, double dx, double dy, double lambda, 
     if ((e = cudaMemset(p->status, 0, sizeof(int))) != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaMemset"); }
     if ((st = ensure_scratch(p, 1))) { free_plan(p); return st; }
     *out = p;
+    return CWO_OK;
+}
+}  // namespace
+
+extern "C" {
+
+const char* cwo_last_error(void) { return g_err.c_str(); }
+
+int cwo_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+cwo_status cwo_plan_device_bytes(int nx, int ny, int batch, size_t* bytes) {
+    if (!bytes) return fail(CWO_ERR_INVALID_ARG, "bytes is NULL");
+    if (!pow2_side(nx) || !pow2_side(ny)) return fail(CWO_ERR_INVALID_ARG, "Nx=%d, Ny=%d out of range", nx, ny);
+    if (batch < 1) return fail(CWO_ERR_INVALID_ARG, "batch must be >= 1");
+    *bytes = tables_bytes(nx, ny) + (size_t)batch * ny * (2 * (size_t)nx) * sizeof(float2);
+    return CWO_OK;
+}
+
+
+cwo_status cwo_plan_create(int nx, int ny, double dx, double dy, double lambda, double z,
+                           cwo_type type, unsigned flags, cwo_plan** out) {
+    if (!out) return fail(CWO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (type == CWO_SHIFTED_ANGULAR)
+        return fail(CWO_ERR_INVALID_ARG, "create shifted angular-spectrum plans with cwo_plan_create_shifted");
+    cwo_status st = check_params(nx, ny, dx, dy, lambda, z, (int)type, flags);
+    if (st) return st;
+    return create_impl(nx, ny, dx, dy, lambda, z, type, flags, nullptr, out);
+}
+
+cwo_status cwo_plan_create_shifted(int nx, int ny, double dx, double dy, double lambda, double z,
+                                   const cwo_shift* shift, unsigned flags, cwo_plan** out) {
+    if (!out) return fail(CWO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!shift) return fail(CWO_ERR_INVALID_ARG, "shift is NULL");
+    cwo_status st = check_params(nx, ny, dx, dy, lambda, z, (int)CWO_ANGULAR, flags);
+    if (st) return st;
+    if (flags & CWO_FLAG_PHASE_FP32) return fail(CWO_ERR_UNSUPPORTED, "CWO_FLAG_PHASE_FP32 is not provided with a shift");
+    const double v[6] = {shift->ox, shift->oy, shift->cx, shift->wx, shift->cy, shift->wy};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(CWO_ERR_INVALID_ARG, "shift and window parameters must be finite");
+    int lo, hi;
+    window_bins(AxisGeo(2 * nx), dx, shift->cx, shift->wx, &lo, &hi);
+    if (lo > hi) return fail(CWO_ERR_INVALID_ARG, "the x window contains no frequency bin");
+    window_bins(AxisGeo(2 * ny), dy, shift->cy, shift->wy, &lo, &hi);
+    if (lo > hi) return fail(CWO_ERR_INVALID_ARG, "the y window contains no frequency bin");
+    return create_impl(nx, ny, dx, dy, lambda, z, CWO_SHIFTED_ANGULAR, flags, shift, out);
+}
+
+cwo_status cwo_band_limit(int nx, int ny, double dx, double dy, double lambda, double z, cwo_shift* out) {
+    if (!out) return fail(CWO_ERR_INVALID_ARG, "out is NULL");
+    cwo_status st = check_params(nx, ny, dx, dy, lambda, z, (int)CWO_ANGULAR, 0);
+    if (st) return st;
+    *out = cwo_shift{};
+    out->wx = 2.0 * band_limit_freq(2 * nx, dx, lambda, z);
+    out->wy = 2.0 * band_limit_freq(2 * ny, dy, lambda, z);
     return CWO_OK;
 }
 
@@ -665,7 +727,8 @@ cwo_status cwo_propagate_epilogue(cwo_plan* plan, const void* in_c64, void* out_
 cwo_status cwo_gs_run(cwo_plan* plan, const float* amplitude, void* field_c64, float* intensity, int batch,
                       int iterations, void* cuda_stream) {
     if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
-    if (plan->type != CWO_ANGULAR) return fail(CWO_ERR_UNSUPPORTED, "the GS iteration uses an angular-spectrum plan");
+    if (plan->type != CWO_ANGULAR && plan->type != CWO_SHIFTED_ANGULAR)
+        return fail(CWO_ERR_UNSUPPORTED, "the GS iteration uses an angular-spectrum plan");
     if (!amplitude || !field_c64) return fail(CWO_ERR_INVALID_ARG, "amplitude and field are required");
     if (iterations < 0 || iterations > 1000000) return fail(CWO_ERR_INVALID_ARG, "iterations must be in [0, 1e6] (got %d)", iterations);
     const long long f = (long long)plan->nx * plan->ny;

@@ -196,6 +196,49 @@ void asm_axis_table(const AxisGeo& g, double pitch, double lambda, double z, boo
     }
 }
 
+bool in_window(double f, double wc, double ww) { return !(ww > 0) || std::fabs(f - wc) <= 0.5 * ww; }
+
+void asm_axis_table_shifted(const AxisGeo& g, double pitch, double lambda, double z, bool is_x, double shift,
+                            double wc, double ww, float4* out) {
+    const double K = z / lambda;
+    const double c0 = is_x ? frac01(K) : 0.0;
+    const double sgn = (is_x && K < 0) ? -1.0 : 1.0;
+    const double rt = std::sqrt(std::fabs(K)) * 0.5;
+    const double Pd = (double)g.P * pitch;
+    const double c1 = z * lambda / (2.0 * Pd * Pd);
+    const double c2 = z * lambda * lambda * lambda / (8.0 * Pd * Pd * Pd * Pd);
+    for (int i = 0; i < g.P; ++i) {
+        const double kt = (double)g.signed_bin(g.freq_of_idx(i));
+        const double f = kt / Pd;
+        if (!in_window(f, wc, ww)) {
+            out[i] = make_float4(2.0f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const double k2 = kt * kt;
+        const double a = lambda * lambda * k2 / (Pd * Pd);
+        // the kernel forms psi = -(W_x + W_y) - ...: subtracting frac(shift f) adds shift f cycles
+        const double W = frac01(frac01(c1 * k2) + frac01(c2 * k2 * k2) + frac01(-shift * f)) - c0;
+        const double u = sgn * rt * a;
+        const float uh = (float)u;
+        const float ul = (float)(u - (double)uh);
+        out[i] = make_float4((float)a, (float)W, uh, ul);
+    }
+}
+
+void window_bins(const AxisGeo& g, double pitch, double wc, double ww, int* lo, int* hi) {
+    const double Pd = (double)g.P * pitch;
+    int l = g.P, h = -g.P - 1;
+    for (int kt = -g.P / 2; kt < g.P / 2; ++kt)
+        if (in_window((double)kt / Pd, wc, ww)) { l = std::min(l, kt); h = std::max(h, kt); }
+    *lo = l;
+    *hi = h;
+}
+
+double band_limit_freq(int p, double pitch, double lambda, double z) {
+    const double df = 1.0 / ((double)p * pitch);
+    return 1.0 / (lambda * std::sqrt((2.0 * df * z) * (2.0 * df * z) + 1.0));
+}
+
 int asm_tail_mode(int px, int py, double dx, double dy, double lambda, double z) {
     (void)px; (void)py;
     const double K = std::fabs(z / lambda);

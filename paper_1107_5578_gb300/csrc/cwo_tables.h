@@ -33,6 +33,16 @@ void fft64(std::vector<cd>& x);
 std::vector<cd> fresnel_axis_dft(int P, double pitch, double lambda, double z);
 cd fresnel_coeff(double dx, double dy, double lambda, double z, bool literal_scale);
 void asm_axis_table(const AxisGeo& g, double pitch, double lambda, double z, bool is_x, float4* out);
+// Shifted ASM (Eq. shift_ang2): the phase gains shift * f cycles (f = kt / (P pitch)), and bins
+// with |f - wc| > ww / 2 (ww > 0) are outside the Rect window: their entry gets a = 2, which the
+// kernel's evanescent test (s > 1) turns into H = 0.  Not symmetric in kt.
+void asm_axis_table_shifted(const AxisGeo& g, double pitch, double lambda, double z, bool is_x, double shift,
+                            double wc, double ww, float4* out);
+// signed-bin interval [lo, hi] of the window |kt / (P pitch) - wc| <= ww / 2 (whole axis if ww <= 0)
+void window_bins(const AxisGeo& g, double pitch, double wc, double ww, int* lo, int* hi);
+// On-axis band limit of the ASM on a padded grid of P = 2N (Matsushima and Shimobaba, Opt.
+// Express 17, 19662 (2009)): |f| <= 1 / (lambda sqrt((2 df z)^2 + 1)), df = 1 / (P pitch).
+double band_limit_freq(int p, double pitch, double lambda, double z);
 
 // transfer-function tables of one parameter set, in axis-index order
 struct HTables {

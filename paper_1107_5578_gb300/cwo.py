@@ -35,6 +35,21 @@ _lock = threading.Lock()
 _lib = None
 
 
+class Shift(ctypes.Structure):
+    """cwo_shift: shift (m) and Rect band-limit windows (centre, full width in 1/m; width <= 0:
+    none) of the shifted angular spectrum method."""
+    _fields_ = [("ox", ctypes.c_double), ("oy", ctypes.c_double), ("cx", ctypes.c_double),
+                ("wx", ctypes.c_double), ("cy", ctypes.c_double), ("wy", ctypes.c_double)]
+
+
+def band_limit(nx: int, ny: int, dx: float, dy: float, wavelength: float, z: float) -> Shift:
+    """The on-axis band-limited ASM windows (no shift) for this geometry."""
+    out = Shift()
+    check(lib().cwo_band_limit(int(nx), int(ny), float(dx), float(dy), float(wavelength), float(z), ctypes.byref(out)),
+          "cwo_band_limit")
+    return out
+
+
 class Item(ctypes.Structure):
     """cwo_item: one entry of a mixed batch (cwo_propagate_items)."""
     _fields_ = [("z", ctypes.c_double), ("wavelength", ctypes.c_double), ("dx", ctypes.c_double),
@@ -63,6 +78,8 @@ def lib() -> ctypes.CDLL:
             sig = {
                 "cwo_plan_create": ([i, i, d, d, d, d, i, u, pp], i),
                 "cwo_plan_destroy": ([vp], i),
+                "cwo_plan_create_shifted": ([i, i, d, d, d, d, ctypes.POINTER(Shift), u, pp], i),
+                "cwo_band_limit": ([i, i, d, d, d, d, ctypes.POINTER(Shift)], i),
                 "cwo_plan_device_bytes": ([i, i, i, sz], i),
                 "cwo_plan_reserve": ([vp, i], i),
                 "cwo_propagate": ([vp, vp, vp, vp], i),
@@ -147,13 +164,20 @@ class Plan:
 
     def __init__(self, nx: int, ny: int | None = None, dx: float = DEFAULT_PITCH,
                  dy: float | None = None, wavelength: float = DEFAULT_WAVELENGTH, z: float = 0.1,
-                 kind: int = ANGULAR, flags: int = 0):
+                 kind: int = ANGULAR, flags: int = 0, shift: "Shift | None" = None):
+        """``shift`` (a Shift) makes a shifted angular-spectrum plan (kind is then SHIFTED_ANGULAR)."""
         self.nx, self.ny = int(nx), int(nx if ny is None else ny)
         self.dx, self.dy = float(dx), float(dx if dy is None else dy)
         self.wavelength, self.z, self.kind, self.flags = float(wavelength), float(z), int(kind), int(flags)
         h = ctypes.c_void_p(0)
-        check(lib().cwo_plan_create(self.nx, self.ny, self.dx, self.dy, self.wavelength, self.z,
-                                    self.kind, self.flags, ctypes.byref(h)), "cwo_plan_create")
+        if shift is not None:
+            self.kind = SHIFTED_ANGULAR
+            check(lib().cwo_plan_create_shifted(self.nx, self.ny, self.dx, self.dy, self.wavelength, self.z,
+                                                ctypes.byref(shift), self.flags, ctypes.byref(h)),
+                  "cwo_plan_create_shifted")
+        else:
+            check(lib().cwo_plan_create(self.nx, self.ny, self.dx, self.dy, self.wavelength, self.z,
+                                        self.kind, self.flags, ctypes.byref(h)), "cwo_plan_create")
         self._h = h
 
     @property

@@ -65,7 +65,7 @@ def test_device_bytes_is_host_only(lib, nx, ny, batch):
     ((16, 16, 1e-5, 1e-5, 633e-9, float("nan"), 0, 0), cwo.ERR_INVALID_ARG),
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 2, 0), cwo.ERR_UNSUPPORTED),       # Fresnel Fourier form
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 3, 0), cwo.ERR_UNSUPPORTED),       # shifted Fresnel
-    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 4, 0), cwo.ERR_UNSUPPORTED),       # shifted ASM
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 4, 0), cwo.ERR_INVALID_ARG),       # shifted ASM: own constructor
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 9, 0), cwo.ERR_INVALID_ARG),       # unknown type
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 0, 0x80), cwo.ERR_INVALID_ARG),    # unknown flag
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 0, 3), cwo.ERR_INVALID_ARG),       # exclusive flags
@@ -161,3 +161,27 @@ def test_host_emulation_of_the_kernels_matches_the_oracle(lib, nx, ny, kind, z, 
     got = cwo.emulate(u.astype(np.complex64), pitch, pitch, 633e-9, z, kind, 0, adjoint)
     want = oracle.propagate(u, pitch, pitch, 633e-9, z, kind, oracle.ADJOINT if adjoint else 0)
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-5
+
+
+@pytest.mark.parametrize("n,dx,lam,z", [(256, 10e-6, 633e-9, 0.5), (512, 4e-6, 532e-9, 0.2), (64, 8e-6, 450e-9, -1.5)])
+def test_band_limit_matches_the_oracle(lib, n, dx, lam, z):
+    import oracle
+    bl = cwo.band_limit(n, n // 2, dx, 1.5 * dx, lam, z)
+    wx, wy = oracle.band_limit(n, n // 2, dx, 1.5 * dx, lam, z)
+    assert abs(bl.wx - wx) <= 1e-12 * wx and abs(bl.wy - wy) <= 1e-12 * wy
+    assert bl.ox == bl.oy == bl.cx == bl.cy == 0.0
+
+
+def test_shifted_plan_argument_checks_need_no_device(lib):
+    empty = cwo.Shift(0.0, 0.0, 1e9, 1.0, 0.0, 0.0)          # window far outside the grid
+    with pytest.raises(cwo.CwoError) as e:
+        cwo.Plan(64, 64, 8e-6, 8e-6, 532e-9, 0.01, shift=empty)
+    assert e.value.status == cwo.ERR_INVALID_ARG
+    bad = cwo.Shift(float("nan"), 0.0, 0.0, 0.0, 0.0, 0.0)
+    with pytest.raises(cwo.CwoError):
+        cwo.Plan(64, 64, 8e-6, 8e-6, 532e-9, 0.01, shift=bad)
+    with pytest.raises(cwo.CwoError) as e:
+        cwo.Plan(64, 64, 8e-6, 8e-6, 532e-9, 0.01, flags=cwo.FLAG_PHASE_FP32, shift=cwo.Shift())
+    assert e.value.status == cwo.ERR_UNSUPPORTED
+    with pytest.raises(cwo.CwoError):
+        cwo.Plan(64, 64, 8e-6, 8e-6, 532e-9, 0.01, kind=cwo.SHIFTED_ANGULAR)   # needs the shifted constructor
