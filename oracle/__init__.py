@@ -22,6 +22,8 @@ Pins (each checked by the ``-m "not gpu"`` tests, none of them by re-calling thi
   * ``propagate_shifted`` -- no shift and no window = ``propagate``; on the circular grid a shift
                           of whole pixels is an exact translation; the window removes the
                           spectrum outside it
+  * ``fresnel_fourier``-- the literal double sum of Eq. fre_fourier3 on tiny grids, the Gaussian
+                          closed form on the destination grid, energy conservation
   * ``band_limit``     -- the limit is where the transfer phase's slope reaches the Nyquist rate
                           of the padded frequency grid (finite differences of the phase)
 """
@@ -296,3 +298,57 @@ def band_limit(nx: int, ny: int, dx: float, dy: float, lam: float, z: float):
     ux = 1.0 / (lam * np.sqrt((2 * dfx * z) ** 2 + 1.0))
     uy = 1.0 / (lam * np.sqrt((2 * dfy * z) ** 2 + 1.0))
     return 2.0 * ux, 2.0 * uy
+
+
+def _centred(n: int) -> np.ndarray:
+    """Centred sample indices m - n/2 of an n-point axis (the array's element n/2 is the axis)."""
+    return np.arange(n) - n // 2
+
+
+def _coeff(dx: float, dy: float, lam: float, z: float, flags: int) -> complex:
+    # exp(i 2 pi z / lam) / (i lam z), with the area element dx dy of the discretised integral
+    # unless LITERAL_SCALE (the same reading as the convolution form)
+    c = np.exp(2j * np.pi * np.fmod(z / lam, 1.0)) / (1j * lam * z)
+    return c if flags & LITERAL_SCALE else c * dx * dy
+
+
+def fresnel_fourier(u1, dx: float, dy: float, lam: float, z: float, flags: int = 0) -> np.ndarray:
+    """Fresnel diffraction in Fourier form (Section "The Fresnel diffraction (Fourier form)",
+    Eqs. fre_fourier2 and fre_fourier3; the y integration variable of Eq. fre_fourier1 read as
+    y1): multiply by the source chirp exp(i pi (x1^2 + y1^2) / (lam z)), take the centred DFT,
+    multiply by C and the destination chirp exp(i pi (x2^2 + y2^2) / (lam z)).  No padding;
+    source coordinates x1 = (m - Nx/2) dx, destination x2 = (k - Nx/2) lam z / (Nx dx) (array
+    element N/2 is the optical axis on both planes).  The centred DFT is computed as
+    fftshift(FFT(ifftshift(.))) with the oracle's own FFT."""
+    u1 = _c128(u1)
+    ny, nx = u1.shape
+    x1 = _centred(nx) * dx
+    y1 = _centred(ny) * dy
+    pre = np.exp(1j * np.pi * (x1[None, :] ** 2 + y1[:, None] ** 2) / (lam * z))
+    g = np.fft.ifftshift(u1 * pre)
+    G = np.fft.fftshift(fft2(g, -1))
+    x2 = _centred(nx) * lam * z / (nx * dx)
+    y2 = _centred(ny) * lam * z / (ny * dy)
+    post = np.exp(1j * np.pi * (x2[None, :] ** 2 + y2[:, None] ** 2) / (lam * z))
+    return _coeff(dx, dy, lam, z, flags) * post * G
+
+
+def fresnel_fourier_direct(u1, dx: float, dy: float, lam: float, z: float, flags: int = 0) -> np.ndarray:
+    """Eq. fre_fourier3 as a literal double sum over the source samples (tiny grids only)."""
+    u1 = _c128(u1)
+    ny, nx = u1.shape
+    x1 = _centred(nx) * dx
+    y1 = _centred(ny) * dy
+    x2 = _centred(nx) * lam * z / (nx * dx)
+    y2 = _centred(ny) * lam * z / (ny * dy)
+    c = _coeff(dx, dy, lam, z, flags)
+    out = np.zeros((ny, nx), dtype=np.complex128)
+    for l in range(ny):
+        for k in range(nx):
+            s = 0j
+            for n in range(ny):
+                for m in range(nx):
+                    s += u1[n, m] * np.exp(1j * np.pi * (x1[m] ** 2 + y1[n] ** 2) / (lam * z)) * \
+                        np.exp(-2j * np.pi * (x2[k] * x1[m] + y2[l] * y1[n]) / (lam * z))
+            out[l, k] = c * np.exp(1j * np.pi * (x2[k] ** 2 + y2[l] ** 2) / (lam * z)) * s
+    return out

@@ -367,3 +367,38 @@ def test_band_limit_is_the_nyquist_rate_of_the_transfer_phase(n, dx, lam, z):
     psi = lambda f: z * np.sqrt(1.0 / lam ** 2 - f ** 2)
     slope = abs(psi(u + h) - psi(u - h)) / (2 * h)
     assert abs(slope * 2 * df - 1.0) < 1e-6
+
+
+# ---------------------------------------------------------------------------------------------
+# Fresnel diffraction, Fourier form (Eqs. fre_fourier2, fre_fourier3)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny,z", [(8, 8, 0.02), (16, 8, -0.05), (8, 4, 0.3)])
+def test_fresnel_fourier_equals_direct_sum(nx, ny, z):
+    u = synth.random_field(nx, seed=41, ny=ny)
+    got = oracle.fresnel_fourier(u, 9e-6, 7e-6, 532e-9, z)
+    want = oracle.fresnel_fourier_direct(u, 9e-6, 7e-6, 532e-9, z)
+    assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_fresnel_fourier_gaussian_closed_form():
+    # the same closed form as the convolution form, sampled on the destination grid
+    # x2 = (k - N/2) lam z / (N dx)
+    n, w0, z = 256, 200e-6, 1.0
+    u = synth.gaussian_beam(n, PITCH, w0)
+    out = oracle.fresnel_fourier(u, PITCH, PITCH, LAM, z)
+    d2 = LAM * z / (n * PITCH)
+    want = _fresnel_gaussian(_grid_r2(n, d2), w0, z)
+    assert np.max(np.abs(out - want)) < 1e-10
+    lit = oracle.fresnel_fourier(u, PITCH, PITCH, LAM, z, flags=oracle.LITERAL_SCALE)
+    assert rel(lit * PITCH * PITCH, out) < 1e-13
+
+
+def test_fresnel_fourier_conserves_energy():
+    # with the area element the discrete transform conserves sum |u|^2 dx dy exactly (DFT Parseval)
+    nx, ny, dx, dy, z = 64, 32, 6e-6, 9e-6, 0.07
+    u = synth.random_field(nx, seed=42, ny=ny)
+    out = oracle.fresnel_fourier(u, dx, dy, LAM, z)
+    dx2, dy2 = LAM * z / (nx * dx), LAM * z / (ny * dy)
+    e1 = np.sum(np.abs(u) ** 2) * dx * dy
+    e2 = np.sum(np.abs(out) ** 2) * dx2 * dy2
+    assert abs(e2 - e1) < 1e-12 * e1
