@@ -30,6 +30,14 @@
  *   - defaults (Section "CWO class", paragraph after Eq. norm): wavelength 633 nm, pitch 10 um;
  *     pass CWO_DEFAULT_WAVELENGTH / CWO_DEFAULT_PITCH to use them
  *
+ *   CWO_FRESNEL_FOURIER  Fresnel diffraction in Fourier form (Section "The Fresnel diffraction
+ *                     (Fourier form)", Eqs. fre_fourier2, fre_fourier3): one UNPADDED Nx x Ny DFT
+ *                       u2 = C exp(i pi (x2^2 + y2^2) / (lambda z)) DFT[u1 exp(i pi (x1^2 + y1^2) / (lambda z))]
+ *                     with centred coordinates on both planes: x1 = (m - Nx/2) dx and
+ *                     x2 = (k - Nx/2) lambda z / (Nx dx) (array element Nx/2 is the axis; the
+ *                     destination pitch is lambda z / (Nx dx), as for y), C as above.  Nx, Ny >= 32;
+ *                     z != 0; forward only (no adjoint, per-item z, stack or epilogue); two passes.
+ *
  * Data layout: fields are complex64 (interleaved float re, im; torch.complex64), row-major
  * [batch][Ny][Nx], contiguous, in DEVICE memory of the current CUDA device.  The caller owns all
  * field buffers; input and output may alias (the input is fully consumed by the first pass before
@@ -68,7 +76,7 @@ extern "C" {
 typedef enum {
     CWO_ANGULAR = 0,          /* angular spectrum method (Eq. ang3)                      */
     CWO_FRESNEL_CONV = 1,     /* Fresnel diffraction, convolution form (Eq. fre_conv_fft) */
-    CWO_FRESNEL_FOURIER = 2,  /* Fourier form (Eq. fre_fourier3): not provided, UNSUPPORTED */
+    CWO_FRESNEL_FOURIER = 2,  /* Fresnel diffraction, Fourier form (Eq. fre_fourier3; below)  */
     CWO_SHIFTED_FRESNEL = 3,  /* shifted Fresnel: not provided, UNSUPPORTED               */
     CWO_SHIFTED_ANGULAR = 4   /* shifted angular spectrum (Eqs. shift_ang1, shift_ang2): plans come
                                  from cwo_plan_create_shifted                             */

@@ -84,6 +84,13 @@ cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2
 // column pass of a shared-source z-stack: one forward transform per column, `planes` outputs
 cudaError_t launch_col_stack(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
                              const float4* tw, const HParams& hp, cudaStream_t st);
+// Fresnel diffraction in Fourier form (cwo_fourier.cu): source chirp + row FFT into the
+// [items][Px = Nx][Ny] intermediate; column FFT + destination chirp into the centred output
+cudaError_t launch_fourier_rows(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap, int ny,
+                                int items, const float2* pre_x, const float2* pre_y, const float4* tw, cudaStream_t st);
+cudaError_t launch_fourier_cols(int py, const float2* win, long long win_item_stride, float2* out, long long out_item_stride,
+                                int nx, int items, const int* st_of_col, const int* row_of_idx, const float2* post_x,
+                                const float2* post_y, const float4* tw, cudaStream_t st);
 // Encode the tensor map of an intermediate [cap][px][ny] at base (host only; no allocation).
 cudaError_t make_intermediate_map(CUtensorMap* map, void* base, int ny, int px, int cap, int rows);
 cudaError_t launch_col(int py, const float2* win, long long win_item_stride, float2* wout,

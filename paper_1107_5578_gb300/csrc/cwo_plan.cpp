@@ -163,6 +163,10 @@ struct cwo_plan {
     // shifted angular spectrum (CWO_SHIFTED_ANGULAR): shift and Rect windows (Eq. shift_ang1)
     bool shifted = false;
     cwo_shift shift{};
+    // Fresnel Fourier form (CWO_FRESNEL_FOURIER): chirps, centring factors, output placement
+    float2* fpre_x = nullptr; float2* fpre_y = nullptr;
+    float2* fpost_x = nullptr; float2* fpost_y = nullptr;
+    int* fst_x = nullptr; int* frow_y = nullptr;
 };
 
 namespace {
@@ -181,6 +185,8 @@ void free_plan(cwo_plan* p) {
     cudaFree(p->ix); cudaFree(p->iy); cudaFree(p->iprm);
     if (p->ihost) cudaFreeHost(p->ihost);
     if (p->iev) cudaEventDestroy(p->iev);
+    cudaFree(p->fpre_x); cudaFree(p->fpre_y); cudaFree(p->fpost_x); cudaFree(p->fpost_y);
+    cudaFree(p->fst_x); cudaFree(p->frow_y);
     delete p;
 }
 
@@ -191,18 +197,22 @@ cwo_status check_params(int nx, int ny, double dx, double dy, double lambda, dou
         return fail(CWO_ERR_INVALID_ARG, "pitches must be finite and > 0 (dx=%g, dy=%g)", dx, dy);
     if (!(lambda > 0) || !std::isfinite(lambda)) return fail(CWO_ERR_INVALID_ARG, "wavelength must be finite and > 0 (%g)", lambda);
     if (!std::isfinite(z)) return fail(CWO_ERR_INVALID_ARG, "distance must be finite (%g)", z);
-    if (type == CWO_FRESNEL_FOURIER || type == CWO_SHIFTED_FRESNEL || type == CWO_SHIFTED_ANGULAR)
-        return fail(CWO_ERR_UNSUPPORTED, "diffraction type %d is not provided (only CWO_ANGULAR and CWO_FRESNEL_CONV)", type);
-    if (type != CWO_ANGULAR && type != CWO_FRESNEL_CONV) return fail(CWO_ERR_INVALID_ARG, "unknown diffraction type %d", type);
-    if (type == CWO_FRESNEL_CONV && z == 0.0) return fail(CWO_ERR_INVALID_ARG, "Fresnel diffraction needs z != 0");
+    if (type == CWO_SHIFTED_FRESNEL || type == CWO_SHIFTED_ANGULAR)
+        return fail(CWO_ERR_UNSUPPORTED, "diffraction type %d is not provided by cwo_plan_create", type);
+    if (type != CWO_ANGULAR && type != CWO_FRESNEL_CONV && type != CWO_FRESNEL_FOURIER)
+        return fail(CWO_ERR_INVALID_ARG, "unknown diffraction type %d", type);
+    if ((type == CWO_FRESNEL_CONV || type == CWO_FRESNEL_FOURIER) && z == 0.0)
+        return fail(CWO_ERR_INVALID_ARG, "Fresnel diffraction needs z != 0");
+    if (type == CWO_FRESNEL_FOURIER && (nx < 32 || ny < 32))
+        return fail(CWO_ERR_INVALID_ARG, "the Fourier form transforms unpadded axes of at least 32 samples (Nx=%d, Ny=%d)", nx, ny);
     const unsigned known = CWO_FLAG_PHASE_FP32 | CWO_FLAG_PHASE_FP64 | CWO_FLAG_LITERAL_SCALE;
     if (flags & ~known) return fail(CWO_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
     if ((flags & CWO_FLAG_PHASE_FP32) && (flags & CWO_FLAG_PHASE_FP64))
         return fail(CWO_ERR_INVALID_ARG, "CWO_FLAG_PHASE_FP32 and CWO_FLAG_PHASE_FP64 are exclusive");
     if ((flags & (CWO_FLAG_PHASE_FP32 | CWO_FLAG_PHASE_FP64)) && type != CWO_ANGULAR)
         return fail(CWO_ERR_INVALID_ARG, "phase-precision flags apply to CWO_ANGULAR only");
-    if ((flags & CWO_FLAG_LITERAL_SCALE) && type != CWO_FRESNEL_CONV)
-        return fail(CWO_ERR_INVALID_ARG, "CWO_FLAG_LITERAL_SCALE applies to CWO_FRESNEL_CONV only");
+    if ((flags & CWO_FLAG_LITERAL_SCALE) && type != CWO_FRESNEL_CONV && type != CWO_FRESNEL_FOURIER)
+        return fail(CWO_ERR_INVALID_ARG, "CWO_FLAG_LITERAL_SCALE applies to the Fresnel types only");
     return CWO_OK;
 }
 
@@ -292,6 +302,12 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
             if (p->type == CWO_FRESNEL_CONV && zs[i] == 0.0) return fail(CWO_ERR_INVALID_ARG, "z[%d] = 0 with Fresnel", i);
         }
     }
+    if (p->type == CWO_FRESNEL_FOURIER) {
+        if (adjoint) return fail(CWO_ERR_UNSUPPORTED, "the adjoint is not provided for the Fourier form");
+        if (zs) return fail(CWO_ERR_UNSUPPORTED, "per-item distances are not provided for the Fourier form");
+        if (stack) return fail(CWO_ERR_UNSUPPORTED, "the shared-source stack is not provided for the Fourier form");
+        if (epi.mode != cwo::EPI_NONE) return fail(CWO_ERR_UNSUPPORTED, "output epilogues are not provided for the Fourier form");
+    }
     cwo_status st = check_plan_device(p);
     if (st) return st;
     const size_t fb = (size_t)field * sizeof(float2);
@@ -308,6 +324,22 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     if ((st = ensure_scratch(p, need))) return st;
 
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->type == CWO_FRESNEL_FOURIER) {
+        const bool timing = p->tev[0] != nullptr;
+        auto mark = [&](int i) { return timing ? cudaEventRecord(p->tev[i], s) : cudaSuccess; };
+        const long long wstride = (long long)p->ny * p->px;
+        cudaError_t e;
+        if ((e = mark(0)) ||
+            (e = cwo::launch_fourier_rows(p->px, (const float2*)in, in_stride, &p->wmap_f, p->ny, batch, p->fpre_x,
+                                          p->fpre_y, p->tw_x, s)) ||
+            (e = mark(1)))
+            return cuda_fail(e, "Fourier-form row launch");
+        if ((e = cwo::launch_fourier_cols(p->py, p->scratch, wstride, (float2*)out, field, p->nx, batch, p->fst_x, p->frow_y,
+                                          p->fpost_x, p->fpost_y, p->tw_y, s)) ||
+            (e = mark(2)) || (e = mark(3)))
+            return cuda_fail(e, "Fourier-form column launch");
+        return CWO_OK;
+    }
     cwo::HParams hp{};
     hp.conj = adjoint ? 1 : 0;
     hp.kbx = p->kb_x;
@@ -574,6 +606,7 @@ cwo_status create_impl(int nx, int ny, double dx, double dy, double lambda, doub
     cwo_plan* p = new (std::nothrow) cwo_plan();
     if (!p) return fail(CWO_ERR_OOM, "host allocation failed");
     p->nx = nx; p->ny = ny; p->px = 2 * nx; p->py = 2 * ny;
+    if (type == CWO_FRESNEL_FOURIER) { p->px = nx; p->py = ny; }   // one unpadded DFT
     p->dx = dx; p->dy = dy; p->lambda = lambda; p->z = z; p->type = type; p->flags = flags;
     if (shift) {
         p->shifted = true;
@@ -596,7 +629,21 @@ cwo_status create_impl(int nx, int ny, double dx, double dy, double lambda, doub
     if ((st = dev_alloc(&p->pairs_x, prs.size(), "x pairs")) || (st = upload(p->pairs_x, prs, "x pair upload"))) { free_plan(p); return st; }
     if ((st = dev_alloc(&p->kb_x, kbx.size(), "x bins")) || (st = upload(p->kb_x, kbx, "x bin upload")) ||
         (st = dev_alloc(&p->kb_y, kby.size(), "y bins")) || (st = upload(p->kb_y, kby, "y bin upload"))) { free_plan(p); return st; }
-    if (type == CWO_ANGULAR || type == CWO_SHIFTED_ANGULAR) {
+    if (type == CWO_FRESNEL_FOURIER) {
+        std::vector<float2> prx(nx), pry(ny), pox(nx), poy(ny);
+        std::vector<int> stx(nx), rwy(ny);
+        fourier_tables(nx, ny, dx, dy, lambda, z, (flags & CWO_FLAG_LITERAL_SCALE) != 0, prx.data(), pry.data(),
+                       pox.data(), poy.data(), stx.data(), rwy.data());
+        if ((st = dev_alloc(&p->fpre_x, prx.size(), "x chirp")) || (st = upload(p->fpre_x, prx, "x chirp upload")) ||
+            (st = dev_alloc(&p->fpre_y, pry.size(), "y chirp")) || (st = upload(p->fpre_y, pry, "y chirp upload")) ||
+            (st = dev_alloc(&p->fpost_x, pox.size(), "x output chirp")) || (st = upload(p->fpost_x, pox, "x output chirp upload")) ||
+            (st = dev_alloc(&p->fpost_y, poy.size(), "y output chirp")) || (st = upload(p->fpost_y, poy, "y output chirp upload")) ||
+            (st = dev_alloc(&p->fst_x, stx.size(), "x placement")) || (st = upload(p->fst_x, stx, "x placement upload")) ||
+            (st = dev_alloc(&p->frow_y, rwy.size(), "y placement")) || (st = upload(p->frow_y, rwy, "y placement upload"))) {
+            free_plan(p);
+            return st;
+        }
+    } else if (type == CWO_ANGULAR || type == CWO_SHIFTED_ANGULAR) {
         std::vector<float4> ax(p->px), ay(p->py);
         std::vector<float> kf(1);
         host_h_tables(p, z, ax.data(), ay.data(), nullptr, nullptr, kf.data());
@@ -749,7 +796,7 @@ cwo_status cwo_gs_run(cwo_plan* plan, const float* amplitude, void* field_c64, f
     return st;
 }
 
-int cwo_launches_per_call(const cwo_plan* plan) { return plan ? 3 : 0; }
+int cwo_launches_per_call(const cwo_plan* plan) { return plan ? (plan->type == CWO_FRESNEL_FOURIER ? 2 : 3) : 0; }
 
 cwo_status cwo_plan_check(cwo_plan* plan) {
     if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");

@@ -239,6 +239,48 @@ double band_limit_freq(int p, double pitch, double lambda, double z) {
     return 1.0 / (lambda * std::sqrt((2.0 * df * z) * (2.0 * df * z) + 1.0));
 }
 
+namespace {
+float2 unit_cycles(double cyc) {
+    const double ph = 2.0 * kPi * frac01(cyc);
+    return make_float2((float)std::cos(ph), (float)std::sin(ph));
+}
+}  // namespace
+
+void fourier_tables(int nx, int ny, double dx, double dy, double lambda, double z, bool literal_scale,
+                    float2* pre_x, float2* pre_y, float2* post_x, float2* post_y, int* st_of_col, int* row_of_idx) {
+    const double lz = lambda * z;
+    for (int m = 0; m < nx; ++m) {
+        const double x = (double)(m - nx / 2) * dx;
+        pre_x[m] = unit_cycles(x * x / (2.0 * lz));
+    }
+    for (int n = 0; n < ny; ++n) {
+        const double y = (double)(n - ny / 2) * dy;
+        pre_y[n] = unit_cycles(y * y / (2.0 * lz));
+    }
+    // C = exp(i 2 pi z / lambda) / (i lambda z) (times dx dy unless literal), in FP64
+    const double cph = 2.0 * kPi * frac01(z / lambda);
+    cd C = cd(std::cos(cph), std::sin(cph)) / cd(0.0, lz);
+    if (!literal_scale) C *= dx * dy;
+    const AxisGeo gx(nx), gy(ny);
+    std::vector<int> where(nx);
+    for (int i = 0; i < nx; ++i) where[gx.freq_of_idx(i)] = i;
+    const double qx = lz / (2.0 * (double)nx * nx * dx * dx);   // cycles per kt^2
+    for (int col = 0; col < nx; ++col) {
+        const int kt = col - nx / 2;
+        const double cyc = frac01(qx * (double)kt * (double)kt) + 0.5 * (double)(kt & 1);
+        const double ph = 2.0 * kPi * frac01(cyc);
+        const double cr = std::cos(ph), ci = std::sin(ph);
+        post_x[col] = make_float2((float)(C.real() * cr - C.imag() * ci), (float)(C.real() * ci + C.imag() * cr));
+        st_of_col[col] = where[(kt + nx) % nx];
+    }
+    const double qy = lz / (2.0 * (double)ny * ny * dy * dy);
+    for (int i = 0; i < ny; ++i) {
+        const int kt = gy.signed_bin(gy.freq_of_idx(i));
+        post_y[i] = unit_cycles(frac01(qy * (double)kt * (double)kt) + 0.5 * (double)(kt & 1));
+        row_of_idx[i] = kt + ny / 2;
+    }
+}
+
 int asm_tail_mode(int px, int py, double dx, double dy, double lambda, double z) {
     (void)px; (void)py;
     const double K = std::fabs(z / lambda);

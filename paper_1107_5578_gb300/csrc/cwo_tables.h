@@ -43,6 +43,15 @@ void window_bins(const AxisGeo& g, double pitch, double wc, double ww, int* lo, 
 // On-axis band limit of the ASM on a padded grid of P = 2N (Matsushima and Shimobaba, Opt.
 // Express 17, 19662 (2009)): |f| <= 1 / (lambda sqrt((2 df z)^2 + 1)), df = 1 / (P pitch).
 double band_limit_freq(int p, double pitch, double lambda, double z);
+// Fresnel diffraction in Fourier form (Eqs. fre_fourier2, fre_fourier3), unpadded Nx x Ny axes:
+//   pre_x[m]     source chirp exp(i pi ((m - Nx/2) dx)^2 / (lambda z))          (natural m)
+//   post_x[col]  C exp(i pi x2^2 / (lambda z)) (-1)^kt, kt = col - Nx/2, x2 = kt lambda z / (Nx dx)
+//   post_y[i]    exp(i pi y2^2 / (lambda z)) (-1)^kt for axis index i of the column FFT
+//   st_of_col    storage column (DIF position) holding the frequency of output column col
+//   row_of_idx   output row (kt + Ny/2) of axis index i
+// every phase reduced modulo one cycle in FP64; (-1)^kt turns the plain DFT into the centred one
+void fourier_tables(int nx, int ny, double dx, double dy, double lambda, double z, bool literal_scale,
+                    float2* pre_x, float2* pre_y, float2* post_x, float2* post_y, int* st_of_col, int* row_of_idx);
 
 // transfer-function tables of one parameter set, in axis-index order
 struct HTables {

@@ -181,6 +181,14 @@ class Plan:
         self._h = h
 
     @property
+    def output_pitch(self) -> tuple:
+        """(dx2, dy2) of the destination plane: the source pitches, except for the Fourier form
+        (lambda z / (Nx dx), lambda z / (Ny dy))."""
+        if self.kind == FRESNEL_FOURIER:
+            return (self.wavelength * self.z / (self.nx * self.dx), self.wavelength * self.z / (self.ny * self.dy))
+        return (self.dx, self.dy)
+
+    @property
     def handle(self) -> ctypes.c_void_p:
         if self._h is None or not self._h.value:
             raise RuntimeError("plan has been destroyed")

@@ -63,7 +63,9 @@ def test_device_bytes_is_host_only(lib, nx, ny, batch):
     ((16, 16, 1e-5, 1e-5, -1.0, 0.1, 0, 0), cwo.ERR_INVALID_ARG),         # negative wavelength
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.0, 1, 0), cwo.ERR_INVALID_ARG),       # Fresnel at z = 0
     ((16, 16, 1e-5, 1e-5, 633e-9, float("nan"), 0, 0), cwo.ERR_INVALID_ARG),
-    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 2, 0), cwo.ERR_UNSUPPORTED),       # Fresnel Fourier form
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 2, 0), cwo.ERR_INVALID_ARG),       # Fourier form needs N >= 32
+    ((32, 32, 1e-5, 1e-5, 633e-9, 0.0, 2, 0), cwo.ERR_INVALID_ARG),       # Fourier form at z = 0
+    ((32, 32, 1e-5, 1e-5, 633e-9, 0.1, 2, 1), cwo.ERR_INVALID_ARG),       # phase flag on the Fourier form
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 3, 0), cwo.ERR_UNSUPPORTED),       # shifted Fresnel
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 4, 0), cwo.ERR_INVALID_ARG),       # shifted ASM: own constructor
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 9, 0), cwo.ERR_INVALID_ARG),       # unknown type
