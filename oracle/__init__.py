@@ -24,6 +24,8 @@ Pins (each checked by the ``-m "not gpu"`` tests, none of them by re-calling thi
                           spectrum outside it
   * ``fresnel_fourier``-- the literal double sum of Eq. fre_fourier3 on tiny grids, the Gaussian
                           closed form on the destination grid, energy conservation
+  * ``shifted_fresnel``-- the literal Fresnel sum at arbitrary destination pitches and offsets,
+                          the convolution form at equal pitches, the off-axis Gaussian closed form
   * ``band_limit``     -- the limit is where the transfer phase's slope reaches the Nyquist rate
                           of the padded frequency grid (finite differences of the phase)
 """
@@ -351,4 +353,63 @@ def fresnel_fourier_direct(u1, dx: float, dy: float, lam: float, z: float, flags
                     s += u1[n, m] * np.exp(1j * np.pi * (x1[m] ** 2 + y1[n] ** 2) / (lam * z)) * \
                         np.exp(-2j * np.pi * (x2[k] * x1[m] + y2[l] * y1[n]) / (lam * z))
             out[l, k] = c * np.exp(1j * np.pi * (x2[k] ** 2 + y2[l] ** 2) / (lam * z)) * s
+    return out
+
+
+def shifted_fresnel(u1, dx0: float, dy0: float, dx1: float, dy1: float, lam: float, z: float,
+                    ox0: float = 0.0, oy0: float = 0.0, ox1: float = 0.0, oy1: float = 0.0,
+                    flags: int = 0) -> np.ndarray:
+    """Shifted Fresnel diffraction (Section "Shifted Fresnel diffraction", Eqs. shift_fre1 to
+    shift_fre3) with source pitch (dx0, dy0) centred at (ox0, oy0) and destination pitch
+    (dx1, dy1) centred at (ox1, oy1): x0 = m0 dx0 + ox0, x1 = m1 dx1 + ox1, m = array index - N/2.
+    Expanding x1 x0 with 2 m1 m0 = m1^2 + m0^2 - (m1 - m0)^2 turns the Fresnel sum into a
+    linear convolution with h_S[d] = exp(i pi S d^2), S = dx0 dx1 / (lam z):
+        u1'[m0] = u1 exp(i pi x0^2 / (lam z)) exp(-2 pi i m0 dx0 ox1 / (lam z)) exp(-i pi S m0^2)
+        u2[m1]  = C exp(i pi x1^2 / (lam z)) exp(-2 pi i ox0 x1 / (lam z)) exp(-i pi S m1^2)
+                  (u1' * h_S)[m1]
+    (per axis, times the y factors), C = exp(i 2 pi z / lam) / (i lam z) dx0 dy0 (LITERAL_SCALE:
+    without dx0 dy0).  The convolution is computed by zero padding to 2N and FFTs with the oracle's
+    FFT, h_S sampled at d = i (i < N) or i - 2N on the padded axis."""
+    u1 = _c128(u1)
+    ny, nx = u1.shape
+    lz = lam * z
+    Sx, Sy = dx0 * dx1 / lz, dy0 * dy1 / lz
+    mx, my = _centred(nx), _centred(ny)
+    x0, y0 = mx * dx0 + ox0, my * dy0 + oy0
+    x1, y1 = mx * dx1 + ox1, my * dy1 + oy1
+    fx = np.exp(1j * np.pi * x0 ** 2 / lz) * np.exp(-2j * np.pi * mx * dx0 * ox1 / lz) * np.exp(-1j * np.pi * Sx * mx ** 2)
+    fy = np.exp(1j * np.pi * y0 ** 2 / lz) * np.exp(-2j * np.pi * my * dy0 * oy1 / lz) * np.exp(-1j * np.pi * Sy * my ** 2)
+    px, py = 2 * nx, 2 * ny
+    g = np.zeros((py, px), dtype=np.complex128)
+    g[:ny, :nx] = u1 * fy[:, None] * fx[None, :]
+    dxs = np.where(np.arange(px) < nx, np.arange(px), np.arange(px) - px)
+    dys = np.where(np.arange(py) < ny, np.arange(py), np.arange(py) - py)
+    h = np.exp(1j * np.pi * Sy * dys[:, None] ** 2) * np.exp(1j * np.pi * Sx * dxs[None, :] ** 2)
+    conv = fft2(fft2(g, -1) * fft2(h, -1), +1)[:ny, :nx] / (px * py)
+    qx = np.exp(1j * np.pi * x1 ** 2 / lz) * np.exp(-2j * np.pi * ox0 * x1 / lz) * np.exp(-1j * np.pi * Sx * mx ** 2)
+    qy = np.exp(1j * np.pi * y1 ** 2 / lz) * np.exp(-2j * np.pi * oy0 * y1 / lz) * np.exp(-1j * np.pi * Sy * my ** 2)
+    c = np.exp(2j * np.pi * np.fmod(z / lam, 1.0)) / (1j * lz)
+    if not flags & LITERAL_SCALE:
+        c = c * dx0 * dy0
+    return c * qy[:, None] * qx[None, :] * conv
+
+
+def fresnel_sum(u1, dx0: float, dy0: float, dx1: float, dy1: float, lam: float, z: float,
+                ox0: float = 0.0, oy0: float = 0.0, ox1: float = 0.0, oy1: float = 0.0) -> np.ndarray:
+    """The Fresnel diffraction integral (Eq. fre_conv) as a literal sum over the source samples,
+    evaluated at every destination sample (tiny grids only): C dx0 dy0 sum u1 exp(i pi ((x1 - x0)^2
+    + (y1 - y0)^2) / (lam z)), coordinates as in shifted_fresnel."""
+    u1 = _c128(u1)
+    ny, nx = u1.shape
+    lz = lam * z
+    x0 = _centred(nx) * dx0 + ox0
+    y0 = _centred(ny) * dy0 + oy0
+    x1 = _centred(nx) * dx1 + ox1
+    y1 = _centred(ny) * dy1 + oy1
+    c = np.exp(2j * np.pi * np.fmod(z / lam, 1.0)) / (1j * lz) * dx0 * dy0
+    out = np.zeros((ny, nx), dtype=np.complex128)
+    for l in range(ny):
+        for k in range(nx):
+            ph = ((x1[k] - x0[None, :]) ** 2 + (y1[l] - y0[:, None]) ** 2) / lz
+            out[l, k] = c * np.sum(u1 * np.exp(1j * np.pi * ph))
     return out

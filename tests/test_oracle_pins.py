@@ -402,3 +402,39 @@ def test_fresnel_fourier_conserves_energy():
     e1 = np.sum(np.abs(u) ** 2) * dx * dy
     e2 = np.sum(np.abs(out) ** 2) * dx2 * dy2
     assert abs(e2 - e1) < 1e-12 * e1
+
+
+# ---------------------------------------------------------------------------------------------
+# Shifted Fresnel diffraction (Eqs. shift_fre1 to shift_fre3)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny,p1,offs,z", [
+    (8, 8, (9e-6, 7e-6), (0, 0, 0, 0), 0.02),
+    (16, 8, (4e-6, 12e-6), (30e-6, -20e-6, 150e-6, 40e-6), 0.05),
+    (8, 16, (20e-6, 5e-6), (-10e-6, 5e-6, -300e-6, 90e-6), -0.1)])
+def test_shifted_fresnel_equals_the_fresnel_sum(nx, ny, p1, offs, z):
+    # the Bluestein rewriting plus padded FFT convolution reproduces the literal Fresnel sum at
+    # arbitrary destination pitches and off-axis positions
+    u = synth.random_field(nx, seed=43, ny=ny)
+    got = oracle.shifted_fresnel(u, 8e-6, 6e-6, p1[0], p1[1], 532e-9, z, *offs)
+    want = oracle.fresnel_sum(u, 8e-6, 6e-6, p1[0], p1[1], 532e-9, z, *offs)
+    assert np.max(np.abs(got - want)) < 1e-11 * np.max(np.abs(want))
+
+
+def test_shifted_fresnel_reduces_to_the_convolution_form():
+    # equal pitches and no offsets: the convolution form (source placed top-left, which only
+    # relabels the shared origin)
+    u = synth.random_field(32, seed=44, ny=16)
+    got = oracle.shifted_fresnel(u, 8e-6, 6e-6, 8e-6, 6e-6, 532e-9, 0.03)
+    want = oracle.propagate(u, 8e-6, 6e-6, 532e-9, 0.03, oracle.FRESNEL_CONV)
+    assert np.max(np.abs(got - want)) < 1e-11 * np.max(np.abs(want))
+
+
+def test_shifted_fresnel_gaussian_off_axis():
+    # a centred Gaussian observed on a finer, shifted destination grid: the closed form at x1
+    n, w0, z = 256, 200e-6, 0.1
+    u = synth.gaussian_beam(n, PITCH, w0)
+    p1, ox1, oy1 = 3e-6, 120e-6, -80e-6
+    out = oracle.shifted_fresnel(u, PITCH, PITCH, p1, p1, LAM, z, 0.0, 0.0, ox1, oy1)
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    r2 = ((x - n / 2) * p1 + ox1) ** 2 + ((y - n / 2) * p1 + oy1) ** 2
+    assert np.max(np.abs(out - _fresnel_gaussian(r2, w0, z))) < 1e-10
