@@ -77,7 +77,8 @@ typedef enum {
     CWO_ANGULAR = 0,          /* angular spectrum method (Eq. ang3)                      */
     CWO_FRESNEL_CONV = 1,     /* Fresnel diffraction, convolution form (Eq. fre_conv_fft) */
     CWO_FRESNEL_FOURIER = 2,  /* Fresnel diffraction, Fourier form (Eq. fre_fourier3; below)  */
-    CWO_SHIFTED_FRESNEL = 3,  /* shifted Fresnel: not provided, UNSUPPORTED               */
+    CWO_SHIFTED_FRESNEL = 3,  /* shifted Fresnel (Eqs. shift_fre1-3): plans come from
+                                 cwo_plan_create_shifted_fresnel                          */
     CWO_SHIFTED_ANGULAR = 4   /* shifted angular spectrum (Eqs. shift_ang1, shift_ang2): plans come
                                  from cwo_plan_create_shifted                             */
 } cwo_type;
@@ -128,6 +129,27 @@ typedef struct {
  * epilogues are.  CWO_ERR_INVALID_ARG for non-finite parameters or a window that holds no bin. */
 cwo_status cwo_plan_create_shifted(int nx, int ny, double dx, double dy, double lambda, double z,
                                    const cwo_shift* shift, unsigned flags, cwo_plan** out);
+
+/* Shifted Fresnel diffraction (Section "Shifted Fresnel diffraction", Eqs. shift_fre1 to
+ * shift_fre3): the Fresnel integral from a source grid of pitch (dx0, dy0) centred at (ox0, oy0)
+ * to a destination grid of pitch (dx1, dy1) centred at (ox1, oy1) (metres; off-axis and
+ * rescaling).  With x0 = m0 dx0 + ox0, x1 = m1 dx1 + ox1, m = array index - N/2 and
+ * S = dx0 dx1 / (lambda z), writing 2 m1 m0 = m1^2 + m0^2 - (m1 - m0)^2 gives
+ *   u2[m1] = C q[m1] sum_m0 u1[m0] f[m0] exp(i pi S (m1 - m0)^2)       (per axis, times y)
+ *   f = exp(i pi x0^2 / (lambda z)) exp(-2 pi i m0 dx0 ox1 / (lambda z)) exp(-i pi S m0^2)
+ *   q = exp(i pi x1^2 / (lambda z)) exp(-2 pi i ox0 x1 / (lambda z)) exp(-i pi S m1^2)
+ * C = exp(i 2 pi z / lambda) / (i lambda z) dx0 dy0 (CWO_FLAG_LITERAL_SCALE: without dx0 dy0).
+ * The sum is the padded convolution path of CWO_FRESNEL_CONV with H = DFT[exp(i pi S d^2)] per
+ * axis; f is applied as the first pass loads the source, q and C as the last pass stores.  The
+ * adjoint (destination -> source) is provided; per-item distances and epilogues are not. */
+typedef struct {
+    double dx1, dy1;   /* destination pitches (> 0)  */
+    double ox0, oy0;   /* source-grid centre         */
+    double ox1, oy1;   /* destination-grid centre    */
+} cwo_shifted_fresnel;
+
+cwo_status cwo_plan_create_shifted_fresnel(int nx, int ny, double dx0, double dy0, double lambda, double z,
+                                           const cwo_shifted_fresnel* params, unsigned flags, cwo_plan** out);
 
 /* The on-axis band-limited angular spectrum method (Matsushima and Shimobaba, Opt. Express 17,
  * 19662 (2009)): fills *out with no shift and windows centred on zero of full width 2 u, where

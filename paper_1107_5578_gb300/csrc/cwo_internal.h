@@ -69,15 +69,26 @@ void set_last_error(const char* msg);
 // boxes of row_block_rows(px, inverse) rows x min(256, Px) columns (one map per pass);
 // item_off is added to the item index.
 int row_block_rows(int px, bool inverse);
-cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap,
-                           int item_off, int ny, int items, const float4* tw, int* status, cudaStream_t st);
+
 // output epilogue of the inverse row pass (see cwo_rows.cu); amp / inten are [items][Ny][Nx]
-enum EpiMode { EPI_NONE = 0, EPI_PHASE = 1, EPI_AMPLITUDE = 2, EPI_INTENSITY = 3 };
+//   EPI_SEPARABLE: out = w * qx[x] * qy[y] (x, y the output column and row; shifted Fresnel)
+enum EpiMode { EPI_NONE = 0, EPI_PHASE = 1, EPI_AMPLITUDE = 2, EPI_INTENSITY = 3, EPI_SEPARABLE = 4 };
 struct Epilogue {
     int mode = EPI_NONE;
     const float* amp = nullptr;
     float* inten = nullptr;
+    const float2* qx = nullptr;
+    const float2* qy = nullptr;
 };
+// optional separable factor of the source, applied as the forward row pass loads it:
+// u(x, y) * fx[x] * fy[y] (shifted Fresnel); both null: none
+struct Prefactor {
+    const float2* fx = nullptr;
+    const float2* fy = nullptr;
+};
+cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap,
+                           int item_off, int ny, int items, const float4* tw, int* status, cudaStream_t st,
+                           const Prefactor& pre = Prefactor());
 cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
                            int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st,
                            const Epilogue& ep = Epilogue());

@@ -163,10 +163,15 @@ struct cwo_plan {
     // shifted angular spectrum (CWO_SHIFTED_ANGULAR): shift and Rect windows (Eq. shift_ang1)
     bool shifted = false;
     cwo_shift shift{};
-    // Fresnel Fourier form (CWO_FRESNEL_FOURIER): chirps, centring factors, output placement
+    // Fresnel Fourier form (CWO_FRESNEL_FOURIER): chirps, centring factors, output placement;
+    // shifted Fresnel (CWO_SHIFTED_FRESNEL): source factors f (fpre), destination factors q
+    // (fpost) and their conjugates for the adjoint (fpre_c = conj q, fpost_c = conj f)
     float2* fpre_x = nullptr; float2* fpre_y = nullptr;
     float2* fpost_x = nullptr; float2* fpost_y = nullptr;
+    float2* fpre_cx = nullptr; float2* fpre_cy = nullptr;
+    float2* fpost_cx = nullptr; float2* fpost_cy = nullptr;
     int* fst_x = nullptr; int* frow_y = nullptr;
+    cwo_shifted_fresnel sfr{};
 };
 
 namespace {
@@ -187,6 +192,7 @@ void free_plan(cwo_plan* p) {
     if (p->iev) cudaEventDestroy(p->iev);
     cudaFree(p->fpre_x); cudaFree(p->fpre_y); cudaFree(p->fpost_x); cudaFree(p->fpost_y);
     cudaFree(p->fst_x); cudaFree(p->frow_y);
+    cudaFree(p->fpre_cx); cudaFree(p->fpre_cy); cudaFree(p->fpost_cx); cudaFree(p->fpost_cy);
     delete p;
 }
 
@@ -302,6 +308,10 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
             if (p->type == CWO_FRESNEL_CONV && zs[i] == 0.0) return fail(CWO_ERR_INVALID_ARG, "z[%d] = 0 with Fresnel", i);
         }
     }
+    if (p->type == CWO_SHIFTED_FRESNEL) {
+        if (zs) return fail(CWO_ERR_UNSUPPORTED, "per-item distances are not provided for shifted Fresnel plans");
+        if (epi.mode != cwo::EPI_NONE) return fail(CWO_ERR_UNSUPPORTED, "output epilogues are not provided for shifted Fresnel plans");
+    }
     if (p->type == CWO_FRESNEL_FOURIER) {
         if (adjoint) return fail(CWO_ERR_UNSUPPORTED, "the adjoint is not provided for the Fourier form");
         if (zs) return fail(CWO_ERR_UNSUPPORTED, "per-item distances are not provided for the Fourier form");
@@ -361,7 +371,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         window_bins(AxisGeo(p->px), p->dx, p->shift.cx, p->shift.wx, &hp.wxlo, &hp.wxhi);
         window_bins(AxisGeo(p->py), p->dy, p->shift.cy, p->shift.wy, &hp.wylo, &hp.wyhi);
     }
-    if (p->type == CWO_FRESNEL_CONV) hp.mode = cwo::HMODE_FRESNEL;
+    if (p->type == CWO_FRESNEL_CONV || p->type == CWO_SHIFTED_FRESNEL) hp.mode = cwo::HMODE_FRESNEL;
     else if (p->flags & CWO_FLAG_PHASE_FP32) hp.mode = cwo::HMODE_ASM_FP32;
     else if (p->flags & CWO_FLAG_PHASE_FP64) hp.mode = cwo::HMODE_ASM_FP64;
     else {
@@ -431,6 +441,15 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     const long long wstride = (long long)p->ny * p->px;
     const bool timing = p->tev[0] != nullptr;
     auto mark = [&](int i) { return timing ? cudaEventRecord(p->tev[i], s) : cudaSuccess; };
+    cwo::Prefactor pre;
+    cwo::Epilogue ep = epi;
+    if (p->type == CWO_SHIFTED_FRESNEL) {   // A = diag(q) conv diag(f);  A^H = diag(f*) conv^H diag(q*)
+        pre.fx = adjoint ? p->fpre_cx : p->fpre_x;
+        pre.fy = adjoint ? p->fpre_cy : p->fpre_y;
+        ep.mode = cwo::EPI_SEPARABLE;
+        ep.qx = adjoint ? p->fpost_cx : p->fpost_x;
+        ep.qy = adjoint ? p->fpost_cy : p->fpost_y;
+    }
     const float2* fin = (const float2*)in;
     float2* fout = (float2*)out;
     cudaError_t e;
@@ -439,7 +458,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         // the shared source: row pass once, then per-plane column and inverse row passes
         float2* w0 = p->scratch;
         float2* wz = p->scratch + wstride;
-        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, 0, &p->wmap_f, 0, p->ny, 1, p->tw_x, p->status, s)) || (e = mark(1)))
+        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, 0, &p->wmap_f, 0, p->ny, 1, p->tw_x, p->status, s, pre)) || (e = mark(1)))
             return cuda_fail(e, "row forward launch");
         if (per_item_k) {
             for (int i = 0; i < batch; ++i) {
@@ -451,11 +470,11 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         } else if ((e = cwo::launch_col_stack(p->py, w0, wz, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2))) {
             return cuda_fail(e, "column launch");
         }
-        if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 1, fout, field, p->ny, batch, scale, p->tw_x, p->status, s)) || (e = mark(3)))
+        if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 1, fout, field, p->ny, batch, scale, p->tw_x, p->status, s, ep)) || (e = mark(3)))
             return cuda_fail(e, "row inverse launch");
     } else {
         const long long istr = in_stride ? in_stride : field;
-        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, istr, &p->wmap_f, 0, p->ny, batch, p->tw_x, p->status, s)) || (e = mark(1)))
+        if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, fin, istr, &p->wmap_f, 0, p->ny, batch, p->tw_x, p->status, s, pre)) || (e = mark(1)))
             return cuda_fail(e, "row forward launch");
         if (per_item_k) {
             for (int i = 0; i < batch; ++i) {
@@ -468,7 +487,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         } else if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, batch, p->tw_y, hp, s)) || (e = mark(2))) {
             return cuda_fail(e, "column launch");
         }
-        if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 0, fout, field, p->ny, batch, scale, p->tw_x, p->status, s, epi)) ||
+        if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 0, fout, field, p->ny, batch, scale, p->tw_x, p->status, s, ep)) ||
             (e = mark(3)))
             return cuda_fail(e, "row inverse launch");
     }
@@ -601,7 +620,7 @@ cwo_status run_items(cwo_plan* p, const void* in, long long in_stride, void* out
 // ------------------------------------------------------------------------------------------
 namespace {
 cwo_status create_impl(int nx, int ny, double dx, double dy, double lambda, double z, cwo_type type, unsigned flags,
-                       const cwo_shift* shift, cwo_plan** out) {
+                       const cwo_shift* shift, cwo_plan** out, const cwo_shifted_fresnel* sfr = nullptr) {
     cwo_status st;
     cwo_plan* p = new (std::nothrow) cwo_plan();
     if (!p) return fail(CWO_ERR_OOM, "host allocation failed");
@@ -612,6 +631,7 @@ cwo_status create_impl(int nx, int ny, double dx, double dy, double lambda, doub
         p->shifted = true;
         p->shift = *shift;
     }
+    if (sfr) p->sfr = *sfr;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaGetDevice"); }
 
@@ -629,7 +649,29 @@ cwo_status create_impl(int nx, int ny, double dx, double dy, double lambda, doub
     if ((st = dev_alloc(&p->pairs_x, prs.size(), "x pairs")) || (st = upload(p->pairs_x, prs, "x pair upload"))) { free_plan(p); return st; }
     if ((st = dev_alloc(&p->kb_x, kbx.size(), "x bins")) || (st = upload(p->kb_x, kbx, "x bin upload")) ||
         (st = dev_alloc(&p->kb_y, kby.size(), "y bins")) || (st = upload(p->kb_y, kby, "y bin upload"))) { free_plan(p); return st; }
-    if (type == CWO_FRESNEL_FOURIER) {
+    if (type == CWO_SHIFTED_FRESNEL) {
+        std::vector<float2> fx(nx), fy(ny), qx(nx), qy(ny), hx(p->px), hy(p->py);
+        const double cph = 2.0 * kPi * frac01(z / lambda);
+        cd C = cd(std::cos(cph), std::sin(cph)) / cd(0.0, lambda * z);
+        if (!(flags & CWO_FLAG_LITERAL_SCALE)) C *= dx * dy;
+        shifted_fresnel_axis(nx, dx, p->sfr.dx1, p->sfr.ox0, p->sfr.ox1, lambda, z, C, fx.data(), qx.data(), hx.data());
+        shifted_fresnel_axis(ny, dy, p->sfr.dy1, p->sfr.oy0, p->sfr.oy1, lambda, z, cd(1.0, 0.0), fy.data(), qy.data(), hy.data());
+        auto conj = [](std::vector<float2> v) { for (auto& a : v) a.y = -a.y; return v; };
+        const std::vector<float2> cqx = conj(qx), cqy = conj(qy), cfx = conj(fx), cfy = conj(fy);
+        if ((st = dev_alloc(&p->fpre_x, nx, "x source factor")) || (st = upload(p->fpre_x, fx, "upload")) ||
+            (st = dev_alloc(&p->fpre_y, ny, "y source factor")) || (st = upload(p->fpre_y, fy, "upload")) ||
+            (st = dev_alloc(&p->fpost_x, nx, "x destination factor")) || (st = upload(p->fpost_x, qx, "upload")) ||
+            (st = dev_alloc(&p->fpost_y, ny, "y destination factor")) || (st = upload(p->fpost_y, qy, "upload")) ||
+            (st = dev_alloc(&p->fpre_cx, nx, "x adjoint factor")) || (st = upload(p->fpre_cx, cqx, "upload")) ||
+            (st = dev_alloc(&p->fpre_cy, ny, "y adjoint factor")) || (st = upload(p->fpre_cy, cqy, "upload")) ||
+            (st = dev_alloc(&p->fpost_cx, nx, "x adjoint factor")) || (st = upload(p->fpost_cx, cfx, "upload")) ||
+            (st = dev_alloc(&p->fpost_cy, ny, "y adjoint factor")) || (st = upload(p->fpost_cy, cfy, "upload")) ||
+            (st = dev_alloc(&p->hx, hx.size(), "x table")) || (st = upload(p->hx, hx, "x table upload")) ||
+            (st = dev_alloc(&p->hy, hy.size(), "y table")) || (st = upload(p->hy, hy, "y table upload"))) {
+            free_plan(p);
+            return st;
+        }
+    } else if (type == CWO_FRESNEL_FOURIER) {
         std::vector<float2> prx(nx), pry(ny), pox(nx), poy(ny);
         std::vector<int> stx(nx), rwy(ny);
         fourier_tables(nx, ny, dx, dy, lambda, z, (flags & CWO_FLAG_LITERAL_SCALE) != 0, prx.data(), pry.data(),
@@ -707,6 +749,20 @@ cwo_status cwo_plan_create_shifted(int nx, int ny, double dx, double dy, double 
     window_bins(AxisGeo(2 * ny), dy, shift->cy, shift->wy, &lo, &hi);
     if (lo > hi) return fail(CWO_ERR_INVALID_ARG, "the y window contains no frequency bin");
     return create_impl(nx, ny, dx, dy, lambda, z, CWO_SHIFTED_ANGULAR, flags, shift, out);
+}
+
+cwo_status cwo_plan_create_shifted_fresnel(int nx, int ny, double dx0, double dy0, double lambda, double z,
+                                           const cwo_shifted_fresnel* sf, unsigned flags, cwo_plan** out) {
+    if (!out) return fail(CWO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!sf) return fail(CWO_ERR_INVALID_ARG, "parameters are NULL");
+    cwo_status st = check_params(nx, ny, dx0, dy0, lambda, z, (int)CWO_FRESNEL_CONV, flags);
+    if (st) return st;
+    if (!(sf->dx1 > 0) || !(sf->dy1 > 0) || !std::isfinite(sf->dx1) || !std::isfinite(sf->dy1))
+        return fail(CWO_ERR_INVALID_ARG, "destination pitches must be finite and > 0");
+    if (!std::isfinite(sf->ox0) || !std::isfinite(sf->oy0) || !std::isfinite(sf->ox1) || !std::isfinite(sf->oy1))
+        return fail(CWO_ERR_INVALID_ARG, "offsets must be finite");
+    return create_impl(nx, ny, dx0, dy0, lambda, z, CWO_SHIFTED_FRESNEL, flags, nullptr, out, sf);
 }
 
 cwo_status cwo_band_limit(int nx, int ny, double dx, double dy, double lambda, double z, cwo_shift* out) {

@@ -43,10 +43,10 @@ __host__ __device__ constexpr size_t row_smem_words() {
 // for which the padded layout is conflict free, and the dense tile [st][r] used by the transposing
 // copies is addressed as e * (R T) + threadIdx.x, i.e. consecutive words across a warp.
 
-template <int P, int R>
+template <int P, int R, bool PRE>
 __global__ void __launch_bounds__(R * (P / 16))
 k_row_fwd(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap wmap,
-          int item_off, const float4* __restrict__ tw) {
+          int item_off, const float4* __restrict__ tw, const Prefactor pre) {
     constexpr int T = P / 16, N = P / 2, NT = R * T;
     constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
     extern __shared__ __align__(1024) float2 sm[];
@@ -59,6 +59,11 @@ k_row_fwd(const float2* __restrict__ in, long long in_item_stride, const __grid_
     for (int e = 0; e < 8; ++e) v[e] = __ldg(src + t + e * T);   // DIF stage-0 positions t + e P/16
 #pragma unroll
     for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);   // zero padding, never loaded
+    if constexpr (PRE) {
+        const float2 fy = __ldg(pre.fy + y0 + r);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = cmul(v[e], cmul(__ldg(pre.fx + t + e * T), fy));
+    }
     fwd_from<P, R, PadLayout<P, R>, 0, 8, 0>(v, sm, r, t, TwTable<P>{tw, t});
     // dense tile [st][r]: register e of (r, t) is storage column st = e T + t of row y0 + r
 #pragma unroll
@@ -88,8 +93,9 @@ __device__ __forceinline__ float2 unit_phase(float2 w) {
 }
 
 template <int EPI>
-__device__ __forceinline__ void epilogue_store(float2* out, const Epilogue& ep, long long idx, float2 w) {
+__device__ __forceinline__ void epilogue_store(float2* out, const Epilogue& ep, long long idx, int x, int y, float2 w) {
     if constexpr (EPI == EPI_NONE) out[idx] = w;
+    else if constexpr (EPI == EPI_SEPARABLE) out[idx] = cmul(w, cmul(__ldg(ep.qx + x), __ldg(ep.qy + y)));
     else if constexpr (EPI == EPI_PHASE) out[idx] = unit_phase(w);
     else if constexpr (EPI == EPI_AMPLITUDE) out[idx] = cscale(unit_phase(w), __ldg(ep.amp + idx));
     else ep.inten[idx] = w.x * w.x + w.y * w.y;
@@ -121,7 +127,7 @@ k_row_inv(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __rest
     inv_from<P, R, PadLayout<P, R>, Geo<P>::NST - 1, 0, 0>(v, sm, r, t, TwTable<P>{tw, t});
     const long long base = item * out_item_stride + (long long)(y0 + r) * N;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) epilogue_store<EPI>(out, ep, base + t + e * T, cscale(v[e], scale));   // crop
+    for (int e = 0; e < 8; ++e) epilogue_store<EPI>(out, ep, base + t + e * T, t + e * T, y0 + r, cscale(v[e], scale));   // crop
 }
 
 // ------------------------------------------------------------------------------------------
@@ -143,10 +149,11 @@ __host__ __device__ constexpr size_t row_fwd_p_smem_bytes() {
     return (row_smem_words<P, R>() + (size_t)R * stage_stride<P, R>()) * sizeof(float2) + sizeof(uint64_t);
 }
 
-template <int P, int R>
+template <int P, int R, bool PRE>
 __global__ void __launch_bounds__(R * (P / 16), 1)
 k_row_fwd_p(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap wmap,
-            int item_off, int groups_per_item, int total_groups, const float4* __restrict__ tw, int* status) {
+            int item_off, int groups_per_item, int total_groups, const float4* __restrict__ tw, int* status,
+            const Prefactor pre) {
     constexpr int T = P / 16, N = P / 2, NT = R * T, SST = stage_stride<P, R>();
     constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
     extern __shared__ __align__(1024) float2 sm[];
@@ -174,6 +181,11 @@ k_row_fwd_p(const float2* __restrict__ in, long long in_item_stride, const __gri
         for (int e = 0; e < 8; ++e) v[e] = stage[r * SST + t + e * T];   // DIF stage-0 positions t + e P/16
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);      // zero padding, never loaded
+        if constexpr (PRE) {
+            const float2 fy = __ldg(pre.fy + (g % groups_per_item) * R + r);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = cmul(v[e], cmul(__ldg(pre.fx + t + e * T), fy));
+        }
         fence_proxy_async_smem();   // these reads of the staging buffer precede the next bulk copy into it
         if (__syncthreads_or(!ok)) break;                                // a copy did not land
         if (threadIdx.x == 0 && g + (int)gridDim.x < total_groups) issue(g + gridDim.x);
@@ -256,7 +268,7 @@ k_row_inv_p(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __re
         const int item = g / groups_per_item, y0 = (g % groups_per_item) * R;
         const long long base = item * out_item_stride + (long long)(y0 + r) * N;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) epilogue_store<EPI>(out, ep, base + t + e * T, cscale(v[e], scale));   // crop
+        for (int e = 0; e < 8; ++e) epilogue_store<EPI>(out, ep, base + t + e * T, t + e * T, y0 + r, cscale(v[e], scale));   // crop
     }
 }
 
@@ -276,9 +288,10 @@ static int persistent_grid(K kernel, int threads, size_t smem, int groups) {
     return std::min(groups, sms * per_sm);
 }
 
-template <int P>
-static cudaError_t row_fwd_impl(const float2* in, long long in_item_stride, const CUtensorMap* wmap,
-                                int item_off, int ny, int items, const float4* tw, int* status, cudaStream_t st) {
+template <int P, bool PRE>
+static cudaError_t row_fwd_impl_t(const float2* in, long long in_item_stride, const CUtensorMap* wmap,
+                                  int item_off, int ny, int items, const float4* tw, int* status, const Prefactor& pre,
+                                  cudaStream_t st) {
     constexpr int R = rows_fwd<P>();
     constexpr int T = P / 16;
     if (ny % R) return cudaErrorInvalidValue;
@@ -286,21 +299,33 @@ static cudaError_t row_fwd_impl(const float2* in, long long in_item_stride, cons
     const bool aligned = ((uintptr_t)in % 16 == 0) && (in_item_stride % 2 == 0);
     if (P >= 512 && aligned) {
         const size_t smem = row_fwd_p_smem_bytes<P, R>();
-        cudaError_t e = ensure_smem(k_row_fwd_p<P, R>, smem);
+        cudaError_t e = ensure_smem(k_row_fwd_p<P, R, PRE>, smem);
         if (e != cudaSuccess) return e;
         const int groups = (ny / R) * items;
-        const int grid = persistent_grid(k_row_fwd_p<P, R>, R * T, smem, groups);
+        const int grid = persistent_grid(k_row_fwd_p<P, R, PRE>, R * T, smem, groups);
         if (grid > 0) {
-            k_row_fwd_p<P, R><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, ny / R, groups, tw, status);
+            k_row_fwd_p<P, R, PRE><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, ny / R, groups, tw,
+                                                              status, pre);
             return cudaGetLastError();
         }
     }
     const size_t smem = row_smem_words<P, R>() * sizeof(float2);
-    cudaError_t e = ensure_smem(k_row_fwd<P, R>, smem);
+    cudaError_t e = ensure_smem(k_row_fwd<P, R, PRE>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / R, items);
-    k_row_fwd<P, R><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, tw);
+    k_row_fwd<P, R, PRE><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, tw, pre);
     return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t row_fwd_impl(const float2* in, long long in_item_stride, const CUtensorMap* wmap,
+                                int item_off, int ny, int items, const float4* tw, int* status, const Prefactor& pre,
+                                cudaStream_t st) {
+    if (pre.fx || pre.fy) {
+        if (!pre.fx || !pre.fy) return cudaErrorInvalidValue;
+        return row_fwd_impl_t<P, true>(in, in_item_stride, wmap, item_off, ny, items, tw, status, pre, st);
+    }
+    return row_fwd_impl_t<P, false>(in, in_item_stride, wmap, item_off, ny, items, tw, status, pre, st);
 }
 
 template <int P, int EPI>
@@ -340,6 +365,8 @@ static cudaError_t row_inv_impl(const CUtensorMap* wmap, int item_off, float2* o
             return row_inv_impl_e<P, EPI_AMPLITUDE>(wmap, item_off, out, out_item_stride, ny, items, scale, tw, status, ep, st);
         case EPI_INTENSITY:
             return row_inv_impl_e<P, EPI_INTENSITY>(wmap, item_off, out, out_item_stride, ny, items, scale, tw, status, ep, st);
+        case EPI_SEPARABLE:
+            return row_inv_impl_e<P, EPI_SEPARABLE>(wmap, item_off, out, out_item_stride, ny, items, scale, tw, status, ep, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -389,9 +416,10 @@ int row_block_rows(int px, bool inverse) {
 }
 
 cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap,
-                           int item_off, int ny, int items, const float4* tw, int* status, cudaStream_t st) {
+                           int item_off, int ny, int items, const float4* tw, int* status, cudaStream_t st,
+                           const Prefactor& pre) {
     switch (px) {
-#define CASE(P) case P: return row_fwd_impl<P>(in, in_item_stride, wmap, item_off, ny, items, tw, status, st);
+#define CASE(P) case P: return row_fwd_impl<P>(in, in_item_stride, wmap, item_off, ny, items, tw, status, pre, st);
         CWO_P_CASES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;

@@ -239,12 +239,41 @@ double band_limit_freq(int p, double pitch, double lambda, double z) {
     return 1.0 / (lambda * std::sqrt((2.0 * df * z) * (2.0 * df * z) + 1.0));
 }
 
+
 namespace {
 float2 unit_cycles(double cyc) {
     const double ph = 2.0 * kPi * frac01(cyc);
     return make_float2((float)std::cos(ph), (float)std::sin(ph));
 }
 }  // namespace
+
+void shifted_fresnel_axis(int n, double p0, double p1, double o0, double o1, double lambda, double z, cd coeff,
+                          float2* f, float2* q, float2* h) {
+    const double lz = lambda * z;
+    const double S = p0 * p1 / lz;
+    for (int a = 0; a < n; ++a) {
+        const double m = (double)(a - n / 2);
+        const double x0 = m * p0 + o0, x1 = m * p1 + o1;
+        const double chirp = frac01(0.5 * S * m * m);
+        f[a] = unit_cycles(frac01(x0 * x0 / (2.0 * lz)) + frac01(-m * p0 * o1 / lz) - chirp);
+        const double ph = 2.0 * kPi * frac01(frac01(x1 * x1 / (2.0 * lz)) + frac01(-o0 * x1 / lz) - chirp);
+        const double cr = std::cos(ph), ci = std::sin(ph);
+        q[a] = make_float2((float)(coeff.real() * cr - coeff.imag() * ci), (float)(coeff.real() * ci + coeff.imag() * cr));
+    }
+    const int P = 2 * n;
+    std::vector<cd> hd(P);
+    for (int d = 0; d <= P / 2; ++d) {   // exp(i pi S d^2) is even in d
+        const double ph = 2.0 * kPi * frac01(0.5 * S * (double)d * (double)d);
+        hd[d] = cd(std::cos(ph), std::sin(ph));
+        if (d > 0 && d < P / 2) hd[P - d] = hd[d];
+    }
+    fft64(hd);
+    const AxisCache& c = axis_cache(P);
+    for (int i = 0; i < P; ++i) {
+        const cd v = hd[c.kabs[i]];
+        h[i] = make_float2((float)v.real(), (float)v.imag());
+    }
+}
 
 void fourier_tables(int nx, int ny, double dx, double dy, double lambda, double z, bool literal_scale,
                     float2* pre_x, float2* pre_y, float2* post_x, float2* post_y, int* st_of_col, int* row_of_idx) {

@@ -50,6 +50,15 @@ double band_limit_freq(int p, double pitch, double lambda, double z);
 //   st_of_col    storage column (DIF position) holding the frequency of output column col
 //   row_of_idx   output row (kt + Ny/2) of axis index i
 // every phase reduced modulo one cycle in FP64; (-1)^kt turns the plain DFT into the centred one
+// Shifted Fresnel (Eqs. shift_fre1 to shift_fre3), per axis of n samples (source pitch p0 centred
+// at o0, destination pitch p1 centred at o1, m = array index - n/2, S = p0 p1 / (lambda z)):
+//   f[a] = exp(i pi x0^2 / (lambda z)) exp(-2 pi i m p0 o1 / (lambda z)) exp(-i pi S m^2)
+//   q[a] = exp(i pi x1^2 / (lambda z)) exp(-2 pi i o0 x1 / (lambda z)) exp(-i pi S m^2)  (times coeff)
+//   h[i] = DFT over the padded axis (2n) of exp(i pi S d^2), d = i (i < n) else i - 2n, at axis
+//          index i (DIF order), made exactly even
+// phases reduced modulo one cycle in FP64; coeff multiplies q (pass 1 for the y axis).
+void shifted_fresnel_axis(int n, double p0, double p1, double o0, double o1, double lambda, double z, cd coeff,
+                          float2* f, float2* q, float2* h);
 void fourier_tables(int nx, int ny, double dx, double dy, double lambda, double z, bool literal_scale,
                     float2* pre_x, float2* pre_y, float2* post_x, float2* post_y, int* st_of_col, int* row_of_idx);
 

@@ -42,6 +42,12 @@ class Shift(ctypes.Structure):
                 ("wx", ctypes.c_double), ("cy", ctypes.c_double), ("wy", ctypes.c_double)]
 
 
+class ShiftedFresnel(ctypes.Structure):
+    """cwo_shifted_fresnel: destination pitches and the centres of both grids (metres)."""
+    _fields_ = [("dx1", ctypes.c_double), ("dy1", ctypes.c_double), ("ox0", ctypes.c_double),
+                ("oy0", ctypes.c_double), ("ox1", ctypes.c_double), ("oy1", ctypes.c_double)]
+
+
 def band_limit(nx: int, ny: int, dx: float, dy: float, wavelength: float, z: float) -> Shift:
     """The on-axis band-limited ASM windows (no shift) for this geometry."""
     out = Shift()
@@ -80,6 +86,7 @@ def lib() -> ctypes.CDLL:
                 "cwo_plan_destroy": ([vp], i),
                 "cwo_plan_create_shifted": ([i, i, d, d, d, d, ctypes.POINTER(Shift), u, pp], i),
                 "cwo_band_limit": ([i, i, d, d, d, d, ctypes.POINTER(Shift)], i),
+                "cwo_plan_create_shifted_fresnel": ([i, i, d, d, d, d, ctypes.POINTER(ShiftedFresnel), u, pp], i),
                 "cwo_plan_device_bytes": ([i, i, i, sz], i),
                 "cwo_plan_reserve": ([vp, i], i),
                 "cwo_propagate": ([vp, vp, vp, vp], i),
@@ -164,13 +171,21 @@ class Plan:
 
     def __init__(self, nx: int, ny: int | None = None, dx: float = DEFAULT_PITCH,
                  dy: float | None = None, wavelength: float = DEFAULT_WAVELENGTH, z: float = 0.1,
-                 kind: int = ANGULAR, flags: int = 0, shift: "Shift | None" = None):
-        """``shift`` (a Shift) makes a shifted angular-spectrum plan (kind is then SHIFTED_ANGULAR)."""
+                 kind: int = ANGULAR, flags: int = 0, shift: "Shift | None" = None,
+                 shifted_fresnel: "ShiftedFresnel | None" = None):
+        """``shift`` (a Shift) makes a shifted angular-spectrum plan (kind SHIFTED_ANGULAR);
+        ``shifted_fresnel`` (a ShiftedFresnel) a shifted Fresnel plan (kind SHIFTED_FRESNEL)."""
         self.nx, self.ny = int(nx), int(nx if ny is None else ny)
         self.dx, self.dy = float(dx), float(dx if dy is None else dy)
         self.wavelength, self.z, self.kind, self.flags = float(wavelength), float(z), int(kind), int(flags)
         h = ctypes.c_void_p(0)
-        if shift is not None:
+        self._sfr = shifted_fresnel
+        if shifted_fresnel is not None:
+            self.kind = SHIFTED_FRESNEL
+            check(lib().cwo_plan_create_shifted_fresnel(self.nx, self.ny, self.dx, self.dy, self.wavelength, self.z,
+                                                        ctypes.byref(shifted_fresnel), self.flags, ctypes.byref(h)),
+                  "cwo_plan_create_shifted_fresnel")
+        elif shift is not None:
             self.kind = SHIFTED_ANGULAR
             check(lib().cwo_plan_create_shifted(self.nx, self.ny, self.dx, self.dy, self.wavelength, self.z,
                                                 ctypes.byref(shift), self.flags, ctypes.byref(h)),
@@ -186,6 +201,8 @@ class Plan:
         (lambda z / (Nx dx), lambda z / (Ny dy))."""
         if self.kind == FRESNEL_FOURIER:
             return (self.wavelength * self.z / (self.nx * self.dx), self.wavelength * self.z / (self.ny * self.dy))
+        if self.kind == SHIFTED_FRESNEL:
+            return (self._sfr.dx1, self._sfr.dy1)
         return (self.dx, self.dy)
 
     @property
