@@ -160,12 +160,15 @@ cwo_status cwo_band_limit(int nx, int ny, double dx, double dy, double lambda, d
 /* Release a plan (NULL is accepted).  The caller must make sure no work using it is pending. */
 cwo_status cwo_plan_destroy(cwo_plan* plan);
 
-/* Device bytes a plan for this shape needs to run `batch` fields at once (tables + scratch),
- * for admission control.  Host-only; touches no device. */
+/* Device bytes a plan for this shape needs to run `batch` fields at once (tables, scratch and
+ * per-item tables, i.e. what cwo_plan_reserve(batch) holds), for admission control.  Host-only;
+ * touches no device. */
 cwo_status cwo_plan_device_bytes(int nx, int ny, int batch, size_t* bytes);
 
-/* Grow the plan's scratch so that batches of up to `batch` fields (or z-stacks of up to `batch`
- * planes) run without allocating.  Synchronises the device when it reallocates. */
+/* Grow the plan's scratch and per-item tables so that batches of up to `batch` fields, z-stacks
+ * of up to `batch` planes and mixed batches of up to `batch` items run without allocating (and
+ * without the device synchronisation a reallocation needs).  Synchronises the device when it
+ * reallocates. */
 cwo_status cwo_plan_reserve(cwo_plan* plan, int batch);
 
 /* One propagation of one [Ny][Nx] field with the plan's own parameters (Eq. ang3 or

@@ -22,6 +22,7 @@
 #include "cwo_fft.cuh"
 #include "cwo_internal.h"
 #include "cwo_h.cuh"
+#include "cwo_launch.cuh"
 
 
 namespace cwo {
@@ -213,11 +214,6 @@ k_col_stack(const float2* __restrict__ win, float2* __restrict__ wout, long long
     }
 }
 
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 template <int P, bool MIXED>
 static cudaError_t col_impl_t(const float2* win, long long win_item_stride, float2* wout,
@@ -229,12 +225,12 @@ static cudaError_t col_impl_t(const float2* win, long long win_item_stride, floa
         constexpr int C = cols_per_block<P>();
         if (px % C != 0) return cudaErrorInvalidValue;
         const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
-        if ((e = set_smem(k_col<P, C, MIXED>, smem))) return e;
+        if ((e = kernel_setup<k_col<P, C, MIXED>>(smem, C * T, nullptr))) return e;
         k_col<P, C, MIXED><<<dim3(px / C, items), C * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
     } else if constexpr (col_paired<P>()) {
         constexpr int CP = cols_per_block<P>();
         const size_t smem = (size_t)PadLayout<P, 2 * CP>::WORDS * sizeof(float2);
-        if ((e = set_smem(k_colp<P, CP, MIXED>, smem))) return e;
+        if ((e = kernel_setup<k_colp<P, CP, MIXED>>(smem, CP * T, nullptr))) return e;
         if (hp.npairs != px / 2 + 1 || !hp.pairs) return cudaErrorInvalidValue;
         const unsigned blocks = (unsigned)((hp.npairs + CP - 1) / CP);
         k_colp<P, CP, MIXED><<<dim3(blocks, items), CP * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
@@ -242,7 +238,7 @@ static cudaError_t col_impl_t(const float2* win, long long win_item_stride, floa
         constexpr int C = cols_per_block<P>();
         if (px % C != 0) return cudaErrorInvalidValue;
         const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
-        if ((e = set_smem(k_col<P, C, MIXED>, smem))) return e;
+        if ((e = kernel_setup<k_col<P, C, MIXED>>(smem, C * T, nullptr))) return e;
         k_col<P, C, MIXED><<<dim3(px / C, items), C * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
     }
     return cudaGetLastError();
@@ -264,7 +260,7 @@ static cudaError_t col_stack_impl(const float2* win, float2* wout, long long wou
     if (px % C != 0) return cudaErrorInvalidValue;
     const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
     cudaError_t e;
-    if ((e = set_smem(k_col_stack<P, C>, smem))) return e;
+    if ((e = kernel_setup<k_col_stack<P, C>>(smem, C * T, nullptr))) return e;
     k_col_stack<P, C><<<px / C, C * T, smem, st>>>(win, wout, wout_item_stride, planes, tw, hp);
     return cudaGetLastError();
 }

@@ -13,6 +13,7 @@
 //             DFT a centred one; the C lanes of a row write C * 8 contiguous bytes.
 #include "cwo_fft.cuh"
 #include "cwo_internal.h"
+#include "cwo_launch.cuh"
 #include "cwo_tma.cuh"
 
 namespace cwo {
@@ -75,11 +76,6 @@ k_fourier_cols(const float2* __restrict__ win, long long win_item_stride, float2
     }
 }
 
-template <typename K>
-static cudaError_t fourier_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 template <int P>
 static cudaError_t fourier_rows_impl(const float2* in, long long in_item_stride, const CUtensorMap* wmap, int ny,
@@ -88,7 +84,7 @@ static cudaError_t fourier_rows_impl(const float2* in, long long in_item_stride,
     constexpr int R = fourier_rows<P>();
     if (ny % R || row_block_rows(P, false) != R) return cudaErrorInvalidValue;   // the map's box height
     const size_t smem = fourier_row_words<P, R>() * sizeof(float2);
-    cudaError_t e = fourier_smem(k_fourier_rows<P, R>, smem);
+    cudaError_t e = kernel_setup<k_fourier_rows<P, R>>(smem, R * (P / 16), nullptr);
     if (e != cudaSuccess) return e;
     k_fourier_rows<P, R><<<dim3(ny / R, items), R * (P / 16), smem, st>>>(in, in_item_stride, *wmap, pre_x, pre_y, tw);
     return cudaGetLastError();
@@ -101,7 +97,7 @@ static cudaError_t fourier_cols_impl(const float2* win, long long win_item_strid
     constexpr int C = kFourierCols;
     if (nx % C) return cudaErrorInvalidValue;
     const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
-    cudaError_t e = fourier_smem(k_fourier_cols<P, C>, smem);
+    cudaError_t e = kernel_setup<k_fourier_cols<P, C>>(smem, C * (P / 16), nullptr);
     if (e != cudaSuccess) return e;
     k_fourier_cols<P, C><<<dim3(nx / C, items), C * (P / 16), smem, st>>>(win, win_item_stride, out, out_item_stride, nx,
                                                                           st_of_col, row_of_idx, post_x, post_y, tw);

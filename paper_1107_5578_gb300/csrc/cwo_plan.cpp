@@ -289,8 +289,11 @@ cwo_status check_plan_device(const cwo_plan* p) {
     return CWO_OK;
 }
 
+// prevalidated: the caller (one API call that propagates the same buffers repeatedly) has
+// already checked these buffers with this plan
 cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int batch,
-               const double* zs, void* stream, bool adjoint, const cwo::Epilogue& epi = cwo::Epilogue()) {
+               const double* zs, void* stream, bool adjoint, const cwo::Epilogue& epi = cwo::Epilogue(),
+               bool prevalidated = false) {
     if (!p) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");
     if (batch < 1 || batch > 65535) return fail(CWO_ERR_INVALID_ARG, "batch must be in [1, 65535] (got %d)", batch);
     const long long field = (long long)p->nx * p->ny;
@@ -318,10 +321,11 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         if (stack) return fail(CWO_ERR_UNSUPPORTED, "the shared-source stack is not provided for the Fourier form");
         if (epi.mode != cwo::EPI_NONE) return fail(CWO_ERR_UNSUPPORTED, "output epilogues are not provided for the Fourier form");
     }
-    cwo_status st = check_plan_device(p);
+    cwo_status st = prevalidated ? CWO_OK : check_plan_device(p);
     if (st) return st;
     const size_t fb = (size_t)field * sizeof(float2);
     const size_t in_bytes = stack ? fb : (size_t)((batch - 1) * (in_stride ? in_stride : field)) * sizeof(float2) + fb;
+    if (!prevalidated) {
     if ((st = check_device_range(in, in_bytes, p->device, "input"))) return st;
     if (epi.mode != cwo::EPI_INTENSITY && (st = check_device_range(out, (size_t)batch * fb, p->device, "output"))) return st;
     if (epi.mode != cwo::EPI_NONE) {
@@ -329,6 +333,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
         const size_t rb = (size_t)batch * field * sizeof(float);
         if (epi.mode == cwo::EPI_AMPLITUDE && (st = check_device_range(epi.amp, rb, p->device, "amplitude"))) return st;
         if (epi.mode == cwo::EPI_INTENSITY && (st = check_device_range(epi.inten, rb, p->device, "intensity"))) return st;
+    }
     }
     const int need = stack ? batch + 1 : batch;
     if ((st = ensure_scratch(p, need))) return st;
@@ -496,6 +501,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
 
 cwo_status ensure_itables(cwo_plan* p, int items) {
     if (items <= p->icap) return CWO_OK;
+    items = std::max(items, std::min(2 * p->icap, 65535));   // grow geometrically: few reallocations
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize before growing item tables");
     cudaFree(p->ix); cudaFree(p->iy); cudaFree(p->iprm);
@@ -716,7 +722,8 @@ cwo_status cwo_plan_device_bytes(int nx, int ny, int batch, size_t* bytes) {
     if (!bytes) return fail(CWO_ERR_INVALID_ARG, "bytes is NULL");
     if (!pow2_side(nx) || !pow2_side(ny)) return fail(CWO_ERR_INVALID_ARG, "Nx=%d, Ny=%d out of range", nx, ny);
     if (batch < 1) return fail(CWO_ERR_INVALID_ARG, "batch must be >= 1");
-    *bytes = tables_bytes(nx, ny) + (size_t)batch * ny * (2 * (size_t)nx) * sizeof(float2);
+    *bytes = tables_bytes(nx, ny) + (size_t)batch * ny * (2 * (size_t)nx) * sizeof(float2) +
+             (size_t)batch * (2 * (size_t)nx + 2 * (size_t)ny) * sizeof(float4) + (size_t)batch * sizeof(cwo::ItemParams);
     return CWO_OK;
 }
 
@@ -785,7 +792,9 @@ cwo_status cwo_plan_reserve(cwo_plan* plan, int batch) {
     if (batch < 1 || batch > 65535) return fail(CWO_ERR_INVALID_ARG, "batch must be in [1, 65535]");
     cwo_status st = check_plan_device(plan);
     if (st) return st;
-    return ensure_scratch(plan, batch + 1);
+    if ((st = ensure_scratch(plan, batch + 1))) return st;
+    // mixed batches (cwo_propagate_items) also need per-item tables and their pinned staging
+    return ensure_itables(plan, batch);
 }
 
 cwo_status cwo_propagate(cwo_plan* plan, const void* in_c64, void* out_c64, void* cuda_stream) {
@@ -841,14 +850,23 @@ cwo_status cwo_gs_run(cwo_plan* plan, const float* amplitude, void* field_c64, f
     am.amp = amplitude;
     in.mode = cwo::EPI_INTENSITY;
     in.inten = intensity;
+    // every buffer is checked once; the loop then re-propagates the same buffers
+    cwo_status st = check_plan_device(plan);
+    if (st) return st;
+    if (batch < 1 || batch > 65535) return fail(CWO_ERR_INVALID_ARG, "batch must be in [1, 65535] (got %d)", batch);
+    const size_t n = (size_t)batch * (size_t)f;
+    if ((st = check_device_range(field_c64, n * sizeof(float2), plan->device, "field")) ||
+        (st = check_device_range(amplitude, n * sizeof(float), plan->device, "amplitude")) ||
+        (intensity && (st = check_device_range(intensity, n * sizeof(float), plan->device, "intensity"))))
+        return st;
     // hologram plane: propagate the object field by +z and keep the phase (the kinoform)
-    cwo_status st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, false, ph);
+    st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, false, ph, true);
     for (int i = 0; i < iterations && st == CWO_OK; ++i) {
         // back to the object plane (conj(H) = H(-z)), amplitude constraint; forward, phase constraint
-        st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, true, am);
-        if (st == CWO_OK) st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, false, ph);
+        st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, true, am, true);
+        if (st == CWO_OK) st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, false, ph, true);
     }
-    if (st == CWO_OK && intensity) st = run(plan, field_c64, f, nullptr, batch, nullptr, cuda_stream, true, in);
+    if (st == CWO_OK && intensity) st = run(plan, field_c64, f, nullptr, batch, nullptr, cuda_stream, true, in, true);
     return st;
 }
 

@@ -21,6 +21,7 @@
 #include "cwo_debug.h"
 #include "cwo_fft.cuh"
 #include "cwo_internal.h"
+#include "cwo_launch.cuh"
 #include "cwo_tma.cuh"
 
 namespace cwo {
@@ -272,21 +273,7 @@ k_row_inv_p(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __re
     }
 }
 
-template <typename K>
-static cudaError_t ensure_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
-// CTAs of a persistent launch: resident CTAs per SM x SMs, at most one per group
-template <typename K>
-static int persistent_grid(K kernel, int threads, size_t smem, int groups) {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
-        return 0;
-    return std::min(groups, sms * per_sm);
-}
 
 template <int P, bool PRE>
 static cudaError_t row_fwd_impl_t(const float2* in, long long in_item_stride, const CUtensorMap* wmap,
@@ -299,10 +286,11 @@ static cudaError_t row_fwd_impl_t(const float2* in, long long in_item_stride, co
     const bool aligned = ((uintptr_t)in % 16 == 0) && (in_item_stride % 2 == 0);
     if (P >= 512 && aligned) {
         const size_t smem = row_fwd_p_smem_bytes<P, R>();
-        cudaError_t e = ensure_smem(k_row_fwd_p<P, R, PRE>, smem);
+        int resident = 0;
+        cudaError_t e = kernel_setup<k_row_fwd_p<P, R, PRE>>(smem, R * T, &resident);
         if (e != cudaSuccess) return e;
         const int groups = (ny / R) * items;
-        const int grid = persistent_grid(k_row_fwd_p<P, R, PRE>, R * T, smem, groups);
+        const int grid = std::min(groups, resident);
         if (grid > 0) {
             k_row_fwd_p<P, R, PRE><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, ny / R, groups, tw,
                                                               status, pre);
@@ -310,7 +298,7 @@ static cudaError_t row_fwd_impl_t(const float2* in, long long in_item_stride, co
         }
     }
     const size_t smem = row_smem_words<P, R>() * sizeof(float2);
-    cudaError_t e = ensure_smem(k_row_fwd<P, R, PRE>, smem);
+    cudaError_t e = kernel_setup<k_row_fwd<P, R, PRE>>(smem, R * T, nullptr);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / R, items);
     k_row_fwd<P, R, PRE><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, tw, pre);
@@ -337,17 +325,18 @@ static cudaError_t row_inv_impl_e(const CUtensorMap* wmap, int item_off, float2*
     const size_t smem = row_smem_words<P, R>() * sizeof(float2) + sizeof(uint64_t);   // tile + mbarrier
     if (ny % R) return cudaErrorInvalidValue;
     if constexpr (kRowInvPersistent && P >= 512) {
-        cudaError_t e = ensure_smem(k_row_inv_p<P, R, EPI>, smem);
+        int resident = 0;
+        cudaError_t e = kernel_setup<k_row_inv_p<P, R, EPI>>(smem, R * T, &resident);
         if (e != cudaSuccess) return e;
         const int groups = (ny / R) * items;
-        const int grid = persistent_grid(k_row_inv_p<P, R, EPI>, R * T, smem, groups);
+        const int grid = std::min(groups, resident);
         if (grid > 0) {
             k_row_inv_p<P, R, EPI><<<grid, R * T, smem, st>>>(*wmap, item_off, out, out_item_stride, ny / R, groups,
                                                               scale, tw, status, ep);
             return cudaGetLastError();
         }
     }
-    cudaError_t e = ensure_smem(k_row_inv<P, R, EPI>, smem);
+    cudaError_t e = kernel_setup<k_row_inv<P, R, EPI>>(smem, R * T, nullptr);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / R, items);
     k_row_inv<P, R, EPI><<<grid, R * T, smem, st>>>(*wmap, item_off, out, out_item_stride, scale, tw, status, ep);
