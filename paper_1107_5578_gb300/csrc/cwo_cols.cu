@@ -122,6 +122,7 @@ template <int P, int C, bool MIXED>
 __global__ void __launch_bounds__(C * (P / 16), col_min_blocks<P>())
 k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
       long long wout_item_stride, const float4* __restrict__ tw, const HParams hp) {
+    pdl_wait();
     constexpr int T = P / 16, NY = P / 2;
     using Lay = PadLayout<P, C>;
     extern __shared__ float2 sm[];
@@ -150,6 +151,7 @@ template <int P, int CP, bool MIXED>
 __global__ void __launch_bounds__(CP * (P / 16), 2)
 k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
        long long wout_item_stride, const float4* __restrict__ tw, const HParams hp) {
+    pdl_wait();
     constexpr int T = P / 16, NY = P / 2;
     using Lay = PadLayout<P, 2 * CP>;
     extern __shared__ float2 sm[];
@@ -188,6 +190,7 @@ template <int P, int C>
 __global__ void __launch_bounds__(C * (P / 16), col_min_blocks<P>())
 k_col_stack(const float2* __restrict__ win, float2* __restrict__ wout, long long wout_item_stride, int nplanes,
             const float4* __restrict__ tw, const HParams hp) {
+    pdl_wait();
     constexpr int T = P / 16, NY = P / 2;
     using Lay = PadLayout<P, C>;
     extern __shared__ float2 sm[];
@@ -226,20 +229,26 @@ static cudaError_t col_impl_t(const float2* win, long long win_item_stride, floa
         if (px % C != 0) return cudaErrorInvalidValue;
         const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
         if ((e = kernel_setup<k_col<P, C, MIXED>>(smem, C * T, nullptr))) return e;
-        k_col<P, C, MIXED><<<dim3(px / C, items), C * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
+        e = pdl_launch(k_col<P, C, MIXED>, dim3(px / C, items), dim3(C * T), smem, st, win, win_item_stride, wout,
+                       wout_item_stride, tw, hp);
+        if (e != cudaSuccess) return e;
     } else if constexpr (col_paired<P>()) {
         constexpr int CP = cols_per_block<P>();
         const size_t smem = (size_t)PadLayout<P, 2 * CP>::WORDS * sizeof(float2);
         if ((e = kernel_setup<k_colp<P, CP, MIXED>>(smem, CP * T, nullptr))) return e;
         if (hp.npairs != px / 2 + 1 || !hp.pairs) return cudaErrorInvalidValue;
         const unsigned blocks = (unsigned)((hp.npairs + CP - 1) / CP);
-        k_colp<P, CP, MIXED><<<dim3(blocks, items), CP * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
+        e = pdl_launch(k_colp<P, CP, MIXED>, dim3(blocks, items), dim3(CP * T), smem, st, win, win_item_stride, wout,
+                       wout_item_stride, tw, hp);
+        if (e != cudaSuccess) return e;
     } else {
         constexpr int C = cols_per_block<P>();
         if (px % C != 0) return cudaErrorInvalidValue;
         const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
         if ((e = kernel_setup<k_col<P, C, MIXED>>(smem, C * T, nullptr))) return e;
-        k_col<P, C, MIXED><<<dim3(px / C, items), C * T, smem, st>>>(win, win_item_stride, wout, wout_item_stride, tw, hp);
+        e = pdl_launch(k_col<P, C, MIXED>, dim3(px / C, items), dim3(C * T), smem, st, win, win_item_stride, wout,
+                       wout_item_stride, tw, hp);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -261,8 +270,7 @@ static cudaError_t col_stack_impl(const float2* win, float2* wout, long long wou
     const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
     cudaError_t e;
     if ((e = kernel_setup<k_col_stack<P, C>>(smem, C * T, nullptr))) return e;
-    k_col_stack<P, C><<<px / C, C * T, smem, st>>>(win, wout, wout_item_stride, planes, tw, hp);
-    return cudaGetLastError();
+    return pdl_launch(k_col_stack<P, C>, dim3(px / C), dim3(C * T), smem, st, win, wout, wout_item_stride, planes, tw, hp);
 }
 
 cudaError_t launch_col_stack(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,

@@ -29,6 +29,7 @@ template <int P, int R>
 __global__ void __launch_bounds__(R * (P / 16))
 k_fourier_rows(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap wmap,
                const float2* __restrict__ pre_x, const float2* __restrict__ pre_y, const float4* __restrict__ tw) {
+    pdl_wait();
     constexpr int T = P / 16, NT = R * T;
     constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
     extern __shared__ __align__(1024) float2 sm[];
@@ -57,6 +58,7 @@ __global__ void __launch_bounds__(C * (P / 16))
 k_fourier_cols(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ out,
                long long out_item_stride, int nx, const int* __restrict__ st_of_col, const int* __restrict__ row_of_idx,
                const float2* __restrict__ post_x, const float2* __restrict__ post_y, const float4* __restrict__ tw) {
+    pdl_wait();
     constexpr int T = P / 16;
     extern __shared__ float2 smc[];
     const int c = threadIdx.x % C, t = threadIdx.x / C;
@@ -86,8 +88,8 @@ static cudaError_t fourier_rows_impl(const float2* in, long long in_item_stride,
     const size_t smem = fourier_row_words<P, R>() * sizeof(float2);
     cudaError_t e = kernel_setup<k_fourier_rows<P, R>>(smem, R * (P / 16), nullptr);
     if (e != cudaSuccess) return e;
-    k_fourier_rows<P, R><<<dim3(ny / R, items), R * (P / 16), smem, st>>>(in, in_item_stride, *wmap, pre_x, pre_y, tw);
-    return cudaGetLastError();
+    return pdl_launch(k_fourier_rows<P, R>, dim3(ny / R, items), dim3(R * (P / 16)), smem, st, in, in_item_stride, *wmap,
+                      pre_x, pre_y, tw);
 }
 
 template <int P>
@@ -99,9 +101,8 @@ static cudaError_t fourier_cols_impl(const float2* win, long long win_item_strid
     const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
     cudaError_t e = kernel_setup<k_fourier_cols<P, C>>(smem, C * (P / 16), nullptr);
     if (e != cudaSuccess) return e;
-    k_fourier_cols<P, C><<<dim3(nx / C, items), C * (P / 16), smem, st>>>(win, win_item_stride, out, out_item_stride, nx,
-                                                                          st_of_col, row_of_idx, post_x, post_y, tw);
-    return cudaGetLastError();
+    return pdl_launch(k_fourier_cols<P, C>, dim3(nx / C, items), dim3(C * (P / 16)), smem, st, win, win_item_stride, out,
+                      out_item_stride, nx, st_of_col, row_of_idx, post_x, post_y, tw);
 }
 
 #define CWO_FOURIER_CASES(X) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)

@@ -6,8 +6,38 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <utility>
 
 namespace cwo {
+
+// Programmatic dependent launch: every hot kernel waits for the grid before it in the stream
+// (griddepcontrol.wait, the first thing it does, so that grid's memory is complete and visible),
+// and is launched with programmatic stream serialisation, so its launch is processed while the
+// previous grid runs.  No kernel triggers its dependents early (griddepcontrol.launch_dependents):
+// measured on GB300, every placement of the trigger cost time (up to 2 us per 2048^2 field) or
+// gained nothing, while the launch overlap alone takes 512^2 propagations from 22.6 to 15.2 us.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// grids of more CTAs than this are launched plainly (many waves: nothing to overlap)
+constexpr unsigned kPdlMaxCtas = 4096;
+
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    const bool pdl = (unsigned long long)grid.x * grid.y * grid.z <= kPdlMaxCtas;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+#endif
 
 constexpr int kMaxDevices = 64;
 

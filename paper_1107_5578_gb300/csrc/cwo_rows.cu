@@ -48,6 +48,7 @@ template <int P, int R, bool PRE>
 __global__ void __launch_bounds__(R * (P / 16))
 k_row_fwd(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap wmap,
           int item_off, const float4* __restrict__ tw, const Prefactor pre) {
+    pdl_wait();
     constexpr int T = P / 16, N = P / 2, NT = R * T;
     constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
     extern __shared__ __align__(1024) float2 sm[];
@@ -106,6 +107,7 @@ template <int P, int R, int EPI>
 __global__ void __launch_bounds__(R * (P / 16))
 k_row_inv(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __restrict__ out,
           long long out_item_stride, float scale, const float4* __restrict__ tw, int* status, const Epilogue ep) {
+    pdl_wait();
     constexpr int T = P / 16, N = P / 2, NT = R * T;
     constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
     extern __shared__ __align__(1024) float2 sm[];
@@ -155,6 +157,7 @@ __global__ void __launch_bounds__(R * (P / 16), 1)
 k_row_fwd_p(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap wmap,
             int item_off, int groups_per_item, int total_groups, const float4* __restrict__ tw, int* status,
             const Prefactor pre) {
+    pdl_wait();
     constexpr int T = P / 16, N = P / 2, NT = R * T, SST = stage_stride<P, R>();
     constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
     extern __shared__ __align__(1024) float2 sm[];
@@ -234,6 +237,7 @@ __global__ void __launch_bounds__(R * (P / 16), row_inv_p_min_blocks<P, R>())
 k_row_inv_p(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __restrict__ out,
             long long out_item_stride, int groups_per_item, int total_groups, float scale,
             const float4* __restrict__ tw, int* status, const Epilogue ep) {
+    pdl_wait();
     constexpr int T = P / 16, N = P / 2, NT = R * T;
     constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
     static_assert(Geo<P>::NST >= 2, "at least two stages");
@@ -292,8 +296,8 @@ static cudaError_t row_fwd_impl_t(const float2* in, long long in_item_stride, co
         const int groups = (ny / R) * items;
         const int grid = std::min(groups, resident);
         if (grid > 0) {
-            k_row_fwd_p<P, R, PRE><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, ny / R, groups, tw,
-                                                              status, pre);
+            return pdl_launch(k_row_fwd_p<P, R, PRE>, dim3(grid), dim3(R * T), smem, st, in, in_item_stride, *wmap,
+                              item_off, ny / R, groups, tw, status, pre);
             return cudaGetLastError();
         }
     }
@@ -301,8 +305,7 @@ static cudaError_t row_fwd_impl_t(const float2* in, long long in_item_stride, co
     cudaError_t e = kernel_setup<k_row_fwd<P, R, PRE>>(smem, R * T, nullptr);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / R, items);
-    k_row_fwd<P, R, PRE><<<grid, R * T, smem, st>>>(in, in_item_stride, *wmap, item_off, tw, pre);
-    return cudaGetLastError();
+    return pdl_launch(k_row_fwd<P, R, PRE>, grid, dim3(R * T), smem, st, in, in_item_stride, *wmap, item_off, tw, pre);
 }
 
 template <int P>
@@ -331,16 +334,16 @@ static cudaError_t row_inv_impl_e(const CUtensorMap* wmap, int item_off, float2*
         const int groups = (ny / R) * items;
         const int grid = std::min(groups, resident);
         if (grid > 0) {
-            k_row_inv_p<P, R, EPI><<<grid, R * T, smem, st>>>(*wmap, item_off, out, out_item_stride, ny / R, groups,
-                                                              scale, tw, status, ep);
+            return pdl_launch(k_row_inv_p<P, R, EPI>, dim3(grid), dim3(R * T), smem, st, *wmap, item_off, out,
+                              out_item_stride, ny / R, groups, scale, tw, status, ep);
             return cudaGetLastError();
         }
     }
     cudaError_t e = kernel_setup<k_row_inv<P, R, EPI>>(smem, R * T, nullptr);
     if (e != cudaSuccess) return e;
     dim3 grid(ny / R, items);
-    k_row_inv<P, R, EPI><<<grid, R * T, smem, st>>>(*wmap, item_off, out, out_item_stride, scale, tw, status, ep);
-    return cudaGetLastError();
+    return pdl_launch(k_row_inv<P, R, EPI>, grid, dim3(R * T), smem, st, *wmap, item_off, out, out_item_stride, scale, tw,
+                      status, ep);
 }
 
 template <int P>
