@@ -183,6 +183,29 @@ def test_asm_2048_full(cwo):
 
 
 @pytest.mark.slow
+def test_asm_2048_batch16_as_benchmarked(cwo):
+    # the benchmark's launch configuration: one batched call of 16 fields of 2048^2 (each field a
+    # random phase rotation of one random field), persistent row passes over 16 x 512 row groups;
+    # two sampled items against the oracle, every item against the first up to its rotation
+    import torch
+    n, b = 2048, 16
+    base = synth.random_field(n, seed=1000)
+    rot = np.exp(2j * np.pi * synth.rng(5).random(b))
+    x = torch.from_numpy((base[None] * rot[:, None, None]).astype(np.complex64)).cuda()
+    plan = cwo.Plan(n, n, 10e-6, 10e-6, 633e-9, 0.05, cwo.ANGULAR)
+    plan.reserve(b)
+    y = plan.propagate_batch(x)
+    plan.check()
+    got = y.cpu().numpy().astype(np.complex128)
+    for k in (0, 11):
+        want = oracle.propagate(x[k].cpu().numpy(), 10e-6, 10e-6, 633e-9, 0.05, oracle.ANGULAR)
+        assert rel(got[k], want) <= TOL
+    # linearity: item k = rot_k / rot_0 * item 0 up to the FP32 rounding of the input rotation
+    for k in range(1, b):
+        assert rel(got[k], got[0] * (rot[k] / rot[0])) <= 2 * TOL
+
+
+@pytest.mark.slow
 def test_fresnel_stack_2048_sampled_planes(cwo):
     # 2048^2 binary mask (p = 0.5) x Gaussian (sigma 400 px), 532 nm, 8 um, 16 planes z in [0.1, 0.4]
     n = 2048
