@@ -113,9 +113,10 @@ template <int P> constexpr int cols_per_block() {
     return c < 1 ? 1 : (c > 16 ? 16 : c);
 }
 template <int P> constexpr int col_min_blocks() { return (P / 16) * cols_per_block<P>() <= 256 ? 2 : 1; }
-// the paired kernel holds 32 values per thread; above P = 4096 it would need more than the 128
-// registers two resident CTAs allow, so the largest size uses the single-column kernel
-template <int P> constexpr bool col_paired() { return P <= 4096; }
+// the paired kernel holds 32 values per thread (128 registers): two 256-thread CTAs per SM up to
+// P = 4096, one 512-thread CTA at P = 8192 (measured 382 us per 4096^2 field vs 488 for the
+// single-column kernel)
+template <int P> constexpr bool col_paired() { return true; }
 
 // single column per transform (used where the paired kernel would not fit in registers)
 template <int P, int C, bool MIXED>
@@ -148,7 +149,7 @@ k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restr
 // -kx.  H depends on kx only through kx^2 (both methods), so the transfer function is evaluated
 // once for both, and the twiddles of each stage are loaded once for both.
 template <int P, int CP, bool MIXED>
-__global__ void __launch_bounds__(CP * (P / 16), 2)
+__global__ void __launch_bounds__(CP * (P / 16), CP * (P / 16) >= 512 ? 1 : 2)
 k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
        long long wout_item_stride, const float4* __restrict__ tw, const HParams hp) {
     pdl_wait();

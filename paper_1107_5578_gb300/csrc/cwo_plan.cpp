@@ -124,6 +124,27 @@ void cwo::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 // ------------------------------------------------------------------------------------------
 // plan
 // ------------------------------------------------------------------------------------------
+// Pinned host staging for per-call tables, K buffers in rotation: a call waits (on the host) only
+// for the upload that used its buffer K calls earlier, so preparing the next call's tables
+// overlaps the GPU work of the previous ones instead of waiting for it.
+struct StagingRing {
+    static constexpr int K = 4;
+    void* buf[K] = {};
+    cudaEvent_t ev[K] = {};
+    bool pending[K] = {};
+    size_t bytes = 0;
+    int next = 0;
+    void release() {
+        for (int k = 0; k < K; ++k) {
+            if (buf[k]) cudaFreeHost(buf[k]);
+            if (ev[k]) cudaEventDestroy(ev[k]);
+            buf[k] = nullptr; ev[k] = nullptr; pending[k] = false;
+        }
+        bytes = 0;
+        next = 0;
+    }
+};
+
 struct cwo_plan {
     int nx = 0, ny = 0, px = 0, py = 0;
     double dx = 0, dy = 0, lambda = 0, z = 0;
@@ -144,14 +165,12 @@ struct cwo_plan {
     float4* zax = nullptr; float4* zay = nullptr;
     float2* zhx = nullptr; float2* zhy = nullptr;
     float* zkf = nullptr;
-    void* zhost = nullptr; size_t zhost_bytes = 0;   // pinned staging
-    cudaEvent_t zev = nullptr; bool zev_pending = false;
+    StagingRing zstage;   // pinned staging of the per-item z tables
     std::vector<double> zs_cached;   // distances whose tables the per-item buffers hold
     // mixed-batch (cwo_propagate_items) per-item tables and parameters
     int icap = 0;
     float4* ix = nullptr; float4* iy = nullptr; cwo::ItemParams* iprm = nullptr;
-    void* ihost = nullptr; size_t ihost_bytes = 0;
-    cudaEvent_t iev = nullptr; bool iev_pending = false;
+    StagingRing istage;   // pinned staging of the mixed-batch tables
     // scratch intermediate [cap][ny][px]
     float2* scratch = nullptr;
     int scap = 0;
@@ -183,13 +202,11 @@ void free_plan(cwo_plan* p) {
     cudaFree(p->kb_x); cudaFree(p->kb_y); cudaFree(p->pairs_x);
     cudaFree(p->ax); cudaFree(p->ay); cudaFree(p->hx); cudaFree(p->hy); cudaFree(p->kf);
     cudaFree(p->zax); cudaFree(p->zay); cudaFree(p->zhx); cudaFree(p->zhy); cudaFree(p->zkf);
-    if (p->zhost) cudaFreeHost(p->zhost);
-    if (p->zev) cudaEventDestroy(p->zev);
+    p->zstage.release();
     cudaFree(p->scratch);
     cudaFree(p->status);
     cudaFree(p->ix); cudaFree(p->iy); cudaFree(p->iprm);
-    if (p->ihost) cudaFreeHost(p->ihost);
-    if (p->iev) cudaEventDestroy(p->iev);
+    p->istage.release();
     cudaFree(p->fpre_x); cudaFree(p->fpre_y); cudaFree(p->fpost_x); cudaFree(p->fpost_y);
     cudaFree(p->fst_x); cudaFree(p->frow_y);
     cudaFree(p->fpre_cx); cudaFree(p->fpre_cy); cudaFree(p->fpost_cx); cudaFree(p->fpost_cy);
@@ -250,6 +267,46 @@ cwo_status ensure_scratch(cwo_plan* p, int items) {
     return CWO_OK;
 }
 
+cwo_status staging_alloc(StagingRing& r, size_t bytes) {
+    r.release();
+    for (int k = 0; k < StagingRing::K; ++k) {
+        cudaError_t e = cudaMallocHost(&r.buf[k], bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            r.buf[k] = nullptr;
+            r.release();
+            return fail(CWO_ERR_OOM, "pinned staging of %zu bytes failed", bytes);
+        }
+        if ((e = cudaEventCreateWithFlags(&r.ev[k], cudaEventDisableTiming)) != cudaSuccess) {
+            r.release();
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    r.bytes = bytes;
+    return CWO_OK;
+}
+
+// the next staging buffer, once the upload that last used it has been consumed
+cwo_status staging_acquire(StagingRing& r, char** buf, int* slot) {
+    const int k = r.next;
+    if (r.pending[k]) {
+        cudaError_t e = cudaEventSynchronize(r.ev[k]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        r.pending[k] = false;
+    }
+    *buf = (char*)r.buf[k];
+    *slot = k;
+    r.next = (k + 1) % StagingRing::K;
+    return CWO_OK;
+}
+
+cwo_status staging_release_after(StagingRing& r, int slot, cudaStream_t s) {
+    cudaError_t e = cudaEventRecord(r.ev[slot], s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    r.pending[slot] = true;
+    return CWO_OK;
+}
+
 cwo_status ensure_ztables(cwo_plan* p, int items) {
     if (items <= p->zcap) return CWO_OK;
     p->zs_cached.clear();
@@ -257,26 +314,22 @@ cwo_status ensure_ztables(cwo_plan* p, int items) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize before growing tables");
     cudaFree(p->zax); cudaFree(p->zay); cudaFree(p->zhx); cudaFree(p->zhy); cudaFree(p->zkf);
     p->zax = p->zay = nullptr; p->zhx = p->zhy = nullptr; p->zkf = nullptr;
-    if (p->zhost) { cudaFreeHost(p->zhost); p->zhost = nullptr; }
+    p->zstage.release();
     p->zcap = 0;
     cwo_status st;
+    size_t zbytes = 0;
     const size_t nx4 = (size_t)items * p->px, ny4 = (size_t)items * p->py;
     if (p->type == CWO_ANGULAR) {
         if ((st = dev_alloc(&p->zax, nx4, "per-item x tables")) || (st = dev_alloc(&p->zay, ny4, "per-item y tables")) ||
             (st = dev_alloc(&p->zkf, (size_t)items, "per-item K")))
             return st;
-        p->zhost_bytes = (nx4 + ny4) * sizeof(float4) + items * sizeof(float);
+        zbytes = (nx4 + ny4) * sizeof(float4) + items * sizeof(float);
     } else {
         if ((st = dev_alloc(&p->zhx, nx4, "per-item x tables")) || (st = dev_alloc(&p->zhy, ny4, "per-item y tables")))
             return st;
-        p->zhost_bytes = (nx4 + ny4) * sizeof(float2);
+        zbytes = (nx4 + ny4) * sizeof(float2);
     }
-    e = cudaMallocHost(&p->zhost, p->zhost_bytes);
-    if (e != cudaSuccess) { cudaGetLastError(); p->zhost = nullptr; return fail(CWO_ERR_OOM, "pinned staging of %zu bytes failed", p->zhost_bytes); }
-    if (!p->zev) {
-        e = cudaEventCreateWithFlags(&p->zev, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-    }
+    if ((st = staging_alloc(p->zstage, zbytes))) return st;
     p->zcap = items;
     return CWO_OK;
 }
@@ -403,12 +456,9 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     } else if (zs && !per_item_k) {
         p->zs_cached.clear();
         if ((st = ensure_ztables(p, batch))) return st;
-        if (p->zev_pending) {   // the staging buffer may still feed the previous upload
-            cudaError_t e = cudaEventSynchronize(p->zev);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-            p->zev_pending = false;
-        }
-        char* hb = (char*)p->zhost;
+        char* hb = nullptr;
+        int zslot = 0;
+        if ((st = staging_acquire(p->zstage, &hb, &zslot))) return st;
         if (p->type == CWO_ANGULAR) {
             float4* hax = (float4*)hb;
             float4* hay = hax + (size_t)batch * p->px;
@@ -434,9 +484,7 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
             hp.hx = p->zhx; hp.hy = p->zhy;
             hp.x_item_stride = p->px; hp.y_item_stride = p->py;
         }
-        cudaError_t e = cudaEventRecord(p->zev, s);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        p->zev_pending = true;
+        if ((st = staging_release_after(p->zstage, zslot, s))) return st;
         p->zs_cached.assign(zs, zs + batch);
     } else {
         hp.ax = p->ax; hp.ay = p->ay; hp.kf = p->kf; hp.hx = p->hx; hp.hy = p->hy;
@@ -506,20 +554,14 @@ cwo_status ensure_itables(cwo_plan* p, int items) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize before growing item tables");
     cudaFree(p->ix); cudaFree(p->iy); cudaFree(p->iprm);
     p->ix = p->iy = nullptr; p->iprm = nullptr;
-    if (p->ihost) { cudaFreeHost(p->ihost); p->ihost = nullptr; }
+    p->istage.release();
     p->icap = 0;
     cwo_status st;
     const size_t nx4 = (size_t)items * p->px, ny4 = (size_t)items * p->py;
     if ((st = dev_alloc(&p->ix, nx4, "item x tables")) || (st = dev_alloc(&p->iy, ny4, "item y tables")) ||
         (st = dev_alloc(&p->iprm, (size_t)items, "item parameters")))
         return st;
-    p->ihost_bytes = (nx4 + ny4) * sizeof(float4) + (size_t)items * sizeof(cwo::ItemParams);
-    e = cudaMallocHost(&p->ihost, p->ihost_bytes);
-    if (e != cudaSuccess) { cudaGetLastError(); p->ihost = nullptr; return fail(CWO_ERR_OOM, "pinned staging of %zu bytes failed", p->ihost_bytes); }
-    if (!p->iev) {
-        e = cudaEventCreateWithFlags(&p->iev, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-    }
+    if ((st = staging_alloc(p->istage, (nx4 + ny4) * sizeof(float4) + (size_t)items * sizeof(cwo::ItemParams)))) return st;
     p->icap = items;
     return CWO_OK;
 }
@@ -566,12 +608,10 @@ cwo_status run_items(cwo_plan* p, const void* in, long long in_stride, void* out
     if ((st = check_device_range(in, (size_t)(batch - 1) * in_stride * sizeof(float2) + fb, p->device, "input"))) return st;
     if ((st = check_device_range(out, (size_t)batch * fb, p->device, "output"))) return st;
     if ((st = ensure_scratch(p, batch)) || (st = ensure_itables(p, batch))) return st;
-    if (p->iev_pending) {
-        cudaError_t e = cudaEventSynchronize(p->iev);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-        p->iev_pending = false;
-    }
-    float4* hx = (float4*)p->ihost;
+    char* hb = nullptr;
+    int islot = 0;
+    if ((st = staging_acquire(p->istage, &hb, &islot))) return st;
+    float4* hx = (float4*)hb;
     float4* hy = hx + (size_t)batch * p->px;
     cwo::ItemParams* hp_items = (cwo::ItemParams*)(hy + (size_t)batch * p->py);
     // per-item FP64 tables, items spread over host threads when there is enough work
@@ -594,10 +634,9 @@ cwo_status run_items(cwo_plan* p, const void* in, long long in_stride, void* out
     cudaError_t e;
     if ((e = cudaMemcpyAsync(p->ix, hx, (size_t)batch * p->px * sizeof(float4), cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(p->iy, hy, (size_t)batch * p->py * sizeof(float4), cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(p->iprm, hp_items, (size_t)batch * sizeof(cwo::ItemParams), cudaMemcpyHostToDevice, s)) ||
-        (e = cudaEventRecord(p->iev, s)))
+        (e = cudaMemcpyAsync(p->iprm, hp_items, (size_t)batch * sizeof(cwo::ItemParams), cudaMemcpyHostToDevice, s)))
         return cuda_fail(e, "item table upload");
-    p->iev_pending = true;
+    if ((st = staging_release_after(p->istage, islot, s))) return st;
 
     cwo::HParams hpar{};
     hpar.mode = cwo::HMODE_ASM_POLY;   // per item, see items

@@ -268,6 +268,11 @@ def make_requests(n_req, seed, rate_hz=2000.0, sizes=synth.SERVING_SIZES, weight
 def latency_stats(requests) -> dict:
     lat = np.array([r.t_done - r.t_arrival for r in requests]) * 1e3
     span = max(r.t_done for r in requests) - min(r.t_arrival for r in requests)
+    sizes = np.array([r.n for r in requests])
+    by_size = {int(n): {"p50_ms": round(float(np.percentile(lat[sizes == n], 50)), 4),
+                        "p99_ms": round(float(np.percentile(lat[sizes == n], 99)), 4)}
+               for n in sorted(set(sizes.tolist()))}
     return {"requests": len(requests), "p50_ms": round(float(np.percentile(lat, 50)), 4),
             "p99_ms": round(float(np.percentile(lat, 99)), 4), "mean_ms": round(float(lat.mean()), 4),
-            "max_ms": round(float(lat.max()), 4), "throughput_rps": round(len(requests) / span, 1)}
+            "max_ms": round(float(lat.max()), 4), "throughput_rps": round(len(requests) / span, 1),
+            "by_size": by_size}
