@@ -63,4 +63,30 @@ cudaError_t kernel_setup(size_t smem, int threads, int* resident_ctas) {
     return cudaSuccess;
 }
 
+// the same for a kernel with compile-time cluster dimensions: the number of its clusters the GPU
+// holds at once
+template <auto Kernel>
+cudaError_t cluster_setup(size_t smem, int threads, int* clusters) {
+    static std::atomic<int> cache[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int c = (dev >= 0 && dev < kMaxDevices) ? cache[dev].load(std::memory_order_acquire) : 0;
+    if (c == 0) {
+        if (smem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        int n = 0;
+        if ((e = cudaOccupancyMaxActiveClusters(&n, Kernel, &cfg)) != cudaSuccess) return e;
+        c = n + 1;
+        if (dev >= 0 && dev < kMaxDevices) cache[dev].store(c, std::memory_order_release);
+    }
+    *clusters = c - 1;
+    return cudaSuccess;
+}
+
 }  // namespace cwo
