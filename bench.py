@@ -208,7 +208,8 @@ def serving_measurement(dev, n_req, rate_hz):
     sizes = synth.SERVING_SIZES
     pools = serving.make_pools(sizes, per_size=4, device=dev)
     server = serving.Server(sizes=sizes, pools=pools, device=dev)
-    server.run(serving.make_requests(400, seed=77, rate_hz=rate_hz))            # warm-up
+    server.warm_up()
+    server.run(serving.make_requests(2000, seed=77, rate_hz=4 * rate_hz))       # warm-up
     reqs = serving.make_requests(n_req, seed=78, rate_hz=rate_hz)
     server.batches = 0
     server.run(reqs)

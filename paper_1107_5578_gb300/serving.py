@@ -210,24 +210,63 @@ class Server:
         s.reqs = reqs
         self.batches += 1
 
+    def warm_up(self) -> None:
+        """Touch every code path a run takes (single and gathered batches of every size) so that
+        no first-use cost (module loading, allocator growth) lands inside a measured run."""
+        for n in self.sizes:
+            pool = self.pools.get(n)
+            if pool is None:
+                continue
+            for s in self.slots[n]:
+                for b in (1, min(2, s.capacity)):
+                    for kind in (cwo.ANGULAR, cwo.FRESNEL_CONV):
+                        reqs = [Request(-1, n, kind, 0.1, 532e-9, 8e-6, pool_index=k) for k in range(b)]
+                        self._launch(s, reqs)
+                        s.event.synchronize()
+                        s.reqs = []
+        self.batches = 0
+
     def run(self, requests: list[Request]) -> float:
-        """Open-loop run: requests are released at their arrival times (seconds from start)."""
+        """Open-loop run: requests are released at their arrival times (seconds from start).
+        Python's cyclic garbage collector is paused for the run (a collection over a large heap
+        would stall the loop for its duration)."""
+        import gc
         requests = sorted(requests, key=lambda r: r.t_arrival)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        i, total, done = 0, len(requests), 0
-        while done < total:
-            now = time.perf_counter() - t0
-            while i < total and requests[i].t_arrival <= now:
-                self.submit(requests[i])
-                i += 1
-            self.dispatch()
-            done += self.poll(time.perf_counter() - t0)
-        return time.perf_counter() - t0
+        gc.collect()
+        was_enabled = gc.isenabled()
+        gc.disable()
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            i, total, done = 0, len(requests), 0
+            while done < total:
+                now = time.perf_counter() - t0
+                while i < total and requests[i].t_arrival <= now:
+                    self.submit(requests[i])
+                    i += 1
+                self.dispatch()
+                done += self.poll(time.perf_counter() - t0)
+            return time.perf_counter() - t0
+        finally:
+            if was_enabled:
+                gc.enable()
 
 
 def serve_serial(requests: list[Request], pools, device="cuda", keep_results=False, plans=None) -> float:
-    """Baseline: one request at a time in arrival order, each propagated alone and waited for."""
+    """Baseline: one request at a time in arrival order, each propagated alone and waited for
+    (garbage collector paused as in Server.run)."""
+    import gc
+    gc.collect()
+    was_enabled = gc.isenabled()
+    gc.disable()
+    try:
+        return _serve_serial(requests, pools, device, keep_results, plans)
+    finally:
+        if was_enabled:
+            gc.enable()
+
+
+def _serve_serial(requests, pools, device, keep_results, plans) -> float:
     requests = sorted(requests, key=lambda r: r.t_arrival)
     dev = torch.device(device)
     plans = {} if plans is None else plans
@@ -272,7 +311,11 @@ def latency_stats(requests) -> dict:
     by_size = {int(n): {"p50_ms": round(float(np.percentile(lat[sizes == n], 50)), 4),
                         "p99_ms": round(float(np.percentile(lat[sizes == n], 99)), 4)}
                for n in sorted(set(sizes.tolist()))}
+    arr = np.array([r.t_arrival for r in requests])
+    slow = np.where(lat > 10.0)[0]
     return {"requests": len(requests), "p50_ms": round(float(np.percentile(lat, 50)), 4),
             "p99_ms": round(float(np.percentile(lat, 99)), 4), "mean_ms": round(float(lat.mean()), 4),
             "max_ms": round(float(lat.max()), 4), "throughput_rps": round(len(requests) / span, 1),
+            "over_10ms": int(len(slow)),
+            "over_10ms_arrivals_s": [round(float(arr[slow[0]]), 3), round(float(arr[slow[-1]]), 3)] if len(slow) else None,
             "by_size": by_size}
