@@ -96,3 +96,28 @@ def test_rejected_items(cwo):
     with pytest.raises(ValueError):
         plan.propagate_items(x, [good])
     plan.check()
+
+
+def test_back_to_back_calls_keep_their_own_tables(cwo):
+    # per-call tables go through a ring of pinned staging buffers: ten calls enqueued without any
+    # synchronisation, each with its own parameters, must each produce its own propagation
+    import torch
+    n = 128
+    u = synth.random_field(n, seed=300)
+    x = torch.from_numpy(u.astype(np.complex64)).cuda().unsqueeze(0)
+    plan = cwo.Plan(n, n, 10e-6, 10e-6, 633e-9, 0.1, cwo.ANGULAR)
+    params = [(k % 2, 0.01 + 0.013 * k, (450e-9, 532e-9, 633e-9)[k % 3], 4e-6 + 5e-7 * k) for k in range(10)]
+    outs = [plan.propagate_items(x, [dict(type=t, z=z, wavelength=lam, dx=p)]) for (t, z, lam, p) in params]
+    zs = [[0.02 + 0.01 * k, 0.05 + 0.02 * k] for k in range(6)]
+    xb = x.expand(2, -1, -1).contiguous()
+    zouts = [plan.propagate_batch(xb, z=z) for z in zs]
+    torch.cuda.synchronize()
+    for (t, z, lam, p), y in zip(params, outs):
+        want = oracle.propagate(u.astype(np.complex64), p, p, lam, z, t)
+        got = y[0].cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= TOL
+    for z, y in zip(zs, zouts):
+        for k in range(2):
+            want = oracle.propagate(u.astype(np.complex64), 10e-6, 10e-6, 633e-9, z[k], oracle.ANGULAR)
+            got = y[k].cpu().numpy().astype(np.complex128)
+            assert np.linalg.norm(got - want) / np.linalg.norm(want) <= TOL
