@@ -227,6 +227,36 @@ def serving_measurement(dev, n_req, rate_hz):
             "continuous": cont, "serial": ser}
 
 
+def once_h_measurement(x, y, steps):
+    """The same 2048^2 ASM batch with the transfer function materialised at plan creation
+    (CWO_FLAG_CACHE_H, the paper's "once-calculation"): propagations/s and per-pass times."""
+    import torch
+    from paper_1107_5578_gb300 import cwo
+    B = x.shape[0]
+    plan = cwo.Plan(N, N, PITCH, PITCH, LAM, Z, cwo.ANGULAR, cwo.FLAG_CACHE_H)
+    plan.reserve(B)
+    for _ in range(3):
+        plan.propagate_batch(x, out=y)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    plan.set_timing_events(ev)
+    pp = np.zeros(3)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(steps):
+        plan.propagate_batch(x, out=y)
+        ev[3].synchronize()
+        pp += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+    b.record()
+    torch.cuda.synchronize()
+    plan.set_timing_events(None)
+    ms = a.elapsed_time(b) / steps
+    plan.close()
+    return {"workload": "asm_2048_pad4096, transfer function cached per plan", "value": round(B / (ms / 1e3), 2),
+            "unit": UNIT, "passes_ms": {k: round(v / steps, 4) for k, v in zip(("row_fwd", "col_fwd_h_inv", "row_inv"), pp)},
+            "cache_bytes": (N + 1) * 2 * N * 8}
+
+
 # Table "Calculation times of the GS algorithm on the CPU and GPUs", 40 iterations, GeForce GTX580
 GS_PAPER_MS_40 = {512: 338.0, 1024: 1.19e3, 2048: 4.65e3}
 
@@ -371,6 +401,7 @@ def main():
                 "d2h": round(host_out.numel() * 8 / (c1.elapsed_time(c2) / 1e3) / 1e9, 1)}
 
     stack = stack_measurement(dev, peaks()[0])
+    once_h = once_h_measurement(x, y, args.steps) if rank == 0 else None
     gs_res = gs_measurement(dev) if rank == 0 else None
     serve = serving_measurement(dev, args.serving_requests, args.serving_rate) \
         if args.serving_requests > 0 and rank == 0 else None
@@ -405,6 +436,7 @@ def main():
                 "copy_gbs": copy_gbs},
         "gpu_launches": plan.launches_per_call * args.steps,
         "fresnel_stack": stack,
+        "asm_once_h": once_h,
         "gs_kinoform": gs_res,
         "serving": serve,
         "serving_4x_rate": serve_high,

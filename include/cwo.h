@@ -96,6 +96,12 @@ typedef enum {
 #define CWO_FLAG_PHASE_FP32    0x1u  /* precision study: evaluate the whole ASM phase in FP32   */
 #define CWO_FLAG_PHASE_FP64    0x2u  /* precision study: literal per-element FP64 ASM phase     */
 #define CWO_FLAG_LITERAL_SCALE 0x4u  /* Fresnel: C without the dx*dy area element              */
+#define CWO_FLAG_CACHE_H       0x8u  /* ASM: materialise H for the plan's own z at creation
+                                        (the paper's "once-calculation", Section "Performance"):
+                                        (Nx + 1) x 2Ny complex64 on the device (67 MB at 2048^2);
+                                        calls with the plan's z read it instead of evaluating
+                                        the phase per element (same values, same results);
+                                        calls with per-item distances evaluate as usual       */
 
 typedef struct cwo_plan cwo_plan;
 

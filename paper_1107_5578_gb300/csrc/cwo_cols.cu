@@ -60,7 +60,12 @@ __device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int co
     } else if (mode == HMODE_ASM_POLY || mode == HMODE_ASM_EXACT) {
         K = __ldg(hp.kf + item * hp.kf_item_stride);
     }
-    if (mode == HMODE_FRESNEL) {
+    if (mode == HMODE_TABLE) {
+        const int j = abs(__ldg(hp.kbx + col));
+        const float2* hc = hp.hcache + (long long)j * hp.hcache_stride + t;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) mul(e, __ldg(hc + e * T));
+    } else if (mode == HMODE_FRESNEL) {
         if (MIXED) {
             const float4 X = __ldg(hp.ax + item * hp.x_item_stride + col);
             const float2 hxc = make_float2(X.x, X.y);
@@ -272,6 +277,25 @@ static cudaError_t col_stack_impl(const float2* win, float2* wout, long long wou
     cudaError_t e;
     if ((e = kernel_setup<k_col_stack<P, C>>(smem, C * T, nullptr))) return e;
     return pdl_launch(k_col_stack<P, C>, dim3(px / C), dim3(C * T), smem, st, win, wout, wout_item_stride, planes, tw, hp);
+}
+
+__global__ void k_build_hcache(float2* __restrict__ out, int py, const HParams hp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= py) return;
+    const int col = __ldg(hp.pairs + j).x;
+    float2 h;
+    if (hp.mode == HMODE_ASM_POLY) h = asm_h_reduced<true>(__ldg(hp.ax + col), __ldg(hp.ay + i), __ldg(hp.kf));
+    else if (hp.mode == HMODE_ASM_EXACT) h = asm_h_reduced<false>(__ldg(hp.ax + col), __ldg(hp.ay + i), __ldg(hp.kf));
+    else if (hp.mode == HMODE_ASM_FP32) h = asm_h_fp32(__ldg(hp.kbx + col), __ldg(hp.kby + i), hp);
+    else h = asm_h_fp64(__ldg(hp.kbx + col), __ldg(hp.kby + i), hp.K, hp.sx, hp.sy);
+    out[(long long)j * py + i] = h;
+}
+
+cudaError_t launch_build_hcache(float2* out, int npairs, int py, const HParams& hp, cudaStream_t st) {
+    if (npairs < 1 || py < 1 || hp.mode > HMODE_ASM_FP64) return cudaErrorInvalidValue;
+    k_build_hcache<<<dim3((unsigned)((py + 255) / 256), (unsigned)npairs), 256, 0, st>>>(out, py, hp);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_col_stack(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,

@@ -13,6 +13,7 @@ enum HMode : int {
     HMODE_ASM_FP32 = 2,      // ASM, whole phase in FP32 (precision-study arm)
     HMODE_ASM_FP64 = 3,      // ASM, literal per-element FP64 phase (reference arm, large K s^3)
     HMODE_FRESNEL = 4,       // Fresnel, separable table product
+    HMODE_TABLE = 5,         // ASM transfer function materialised per plan ("once-calculation")
 };
 
 // Per-item parameters of a mixed batch (cwo_propagate_items): the item's transfer-function mode
@@ -58,6 +59,9 @@ struct HParams {
     int asym;
     double shx, shy;
     int wxlo, wxhi, wylo, wyhi;
+    // HMODE_TABLE: H of mirror pair j = |kt_x| at axis index i along y is hcache[j * py + i]
+    const float2* hcache;
+    long long hcache_stride;
 };
 
 // launchers (return cudaGetLastError() after the launch)
@@ -95,6 +99,10 @@ cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2
 // column pass of a shared-source z-stack: one forward transform per column, `planes` outputs
 cudaError_t launch_col_stack(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
                              const float4* tw, const HParams& hp, cudaStream_t st);
+// Materialise the ASM transfer function of hp (modes POLY, EXACT, FP32, FP64 with the plan's
+// own tables) for every mirror pair j = 0 .. npairs-1 and axis index i < py: out[j * py + i],
+// evaluated by the same device functions as the column pass.
+cudaError_t launch_build_hcache(float2* out, int npairs, int py, const HParams& hp, cudaStream_t st);
 // Fresnel diffraction in Fourier form (cwo_fourier.cu): source chirp + row FFT into the
 // [items][Px = Nx][Ny] intermediate; column FFT + destination chirp into the centred output
 cudaError_t launch_fourier_rows(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap, int ny,

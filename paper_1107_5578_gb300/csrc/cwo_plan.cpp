@@ -191,6 +191,8 @@ struct cwo_plan {
     float2* fpost_cx = nullptr; float2* fpost_cy = nullptr;
     int* fst_x = nullptr; int* frow_y = nullptr;
     cwo_shifted_fresnel sfr{};
+    // CWO_FLAG_CACHE_H: the ASM transfer function of the plan's own z, [Px/2 + 1 pairs][Py]
+    float2* hcache = nullptr;
 };
 
 namespace {
@@ -210,6 +212,7 @@ void free_plan(cwo_plan* p) {
     cudaFree(p->fpre_x); cudaFree(p->fpre_y); cudaFree(p->fpost_x); cudaFree(p->fpost_y);
     cudaFree(p->fst_x); cudaFree(p->frow_y);
     cudaFree(p->fpre_cx); cudaFree(p->fpre_cy); cudaFree(p->fpost_cx); cudaFree(p->fpost_cy);
+    cudaFree(p->hcache);
     delete p;
 }
 
@@ -228,7 +231,9 @@ cwo_status check_params(int nx, int ny, double dx, double dy, double lambda, dou
         return fail(CWO_ERR_INVALID_ARG, "Fresnel diffraction needs z != 0");
     if (type == CWO_FRESNEL_FOURIER && (nx < 32 || ny < 32))
         return fail(CWO_ERR_INVALID_ARG, "the Fourier form transforms unpadded axes of at least 32 samples (Nx=%d, Ny=%d)", nx, ny);
-    const unsigned known = CWO_FLAG_PHASE_FP32 | CWO_FLAG_PHASE_FP64 | CWO_FLAG_LITERAL_SCALE;
+    const unsigned known = CWO_FLAG_PHASE_FP32 | CWO_FLAG_PHASE_FP64 | CWO_FLAG_LITERAL_SCALE | CWO_FLAG_CACHE_H;
+    if ((flags & CWO_FLAG_CACHE_H) && type != CWO_ANGULAR)
+        return fail(CWO_ERR_INVALID_ARG, "CWO_FLAG_CACHE_H applies to CWO_ANGULAR plans only");
     if (flags & ~known) return fail(CWO_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
     if ((flags & CWO_FLAG_PHASE_FP32) && (flags & CWO_FLAG_PHASE_FP64))
         return fail(CWO_ERR_INVALID_ARG, "CWO_FLAG_PHASE_FP32 and CWO_FLAG_PHASE_FP64 are exclusive");
@@ -342,6 +347,42 @@ cwo_status check_plan_device(const cwo_plan* p) {
     return CWO_OK;
 }
 
+// launch parameters of the transfer function with the plan's own tables: geometry, the shifted
+// ASM's shift and windows, and the evaluation mode (for the distances zs, or the plan's z)
+cwo::HParams base_hparams(const cwo_plan* p, const double* zs, int batch) {
+    cwo::HParams hp{};
+    hp.kbx = p->kb_x;
+    hp.kby = p->kb_y;
+    hp.pairs = p->pairs_x;
+    hp.npairs = p->px / 2 + 1;
+    hp.K = p->z / p->lambda;
+    hp.sx = p->lambda * p->lambda / ((double)p->px * p->dx * (double)p->px * p->dx);
+    hp.sy = p->lambda * p->lambda / ((double)p->py * p->dy * (double)p->py * p->dy);
+    hp.z = p->z;
+    hp.k = 2.0 * kPi / p->lambda;
+    hp.dfx = 1.0 / ((double)p->px * p->dx);
+    hp.dfy = 1.0 / ((double)p->py * p->dy);
+    if (p->shifted) {
+        hp.asym = 1;
+        hp.shx = p->shift.ox * hp.dfx;
+        hp.shy = p->shift.oy * hp.dfy;
+        window_bins(AxisGeo(p->px), p->dx, p->shift.cx, p->shift.wx, &hp.wxlo, &hp.wxhi);
+        window_bins(AxisGeo(p->py), p->dy, p->shift.cy, p->shift.wy, &hp.wylo, &hp.wyhi);
+    }
+    if (p->type == CWO_FRESNEL_CONV || p->type == CWO_SHIFTED_FRESNEL) hp.mode = cwo::HMODE_FRESNEL;
+    else if (p->flags & CWO_FLAG_PHASE_FP32) hp.mode = cwo::HMODE_ASM_FP32;
+    else if (p->flags & CWO_FLAG_PHASE_FP64) hp.mode = cwo::HMODE_ASM_FP64;
+    else {
+        // the cheapest per-element remainder evaluation that stays within its error budget
+        int tm = 0;
+        if (zs) for (int i = 0; i < batch; ++i) tm = std::max(tm, asm_tail_mode(p->px, p->py, p->dx, p->dy, p->lambda, zs[i]));
+        else tm = asm_tail_mode(p->px, p->py, p->dx, p->dy, p->lambda, p->z);
+        hp.mode = tm == 0 ? cwo::HMODE_ASM_POLY : tm == 1 ? cwo::HMODE_ASM_EXACT : cwo::HMODE_ASM_FP64;
+    }
+    hp.ax = p->ax; hp.ay = p->ay; hp.kf = p->kf; hp.hx = p->hx; hp.hy = p->hy;
+    return hp;
+}
+
 // prevalidated: the caller (one API call that propagates the same buffers repeatedly) has
 // already checked these buffers with this plan
 cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int batch,
@@ -408,37 +449,8 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
             return cuda_fail(e, "Fourier-form column launch");
         return CWO_OK;
     }
-    cwo::HParams hp{};
+    cwo::HParams hp = base_hparams(p, zs, batch);
     hp.conj = adjoint ? 1 : 0;
-    hp.kbx = p->kb_x;
-    hp.kby = p->kb_y;
-    hp.pairs = p->pairs_x;
-    hp.npairs = p->px / 2 + 1;
-    const double K = p->z / p->lambda;
-    hp.K = K;
-    hp.sx = p->lambda * p->lambda / ((double)p->px * p->dx * (double)p->px * p->dx);
-    hp.sy = p->lambda * p->lambda / ((double)p->py * p->dy * (double)p->py * p->dy);
-    hp.z = p->z;
-    hp.k = 2.0 * kPi / p->lambda;
-    hp.dfx = 1.0 / ((double)p->px * p->dx);
-    hp.dfy = 1.0 / ((double)p->py * p->dy);
-    if (p->shifted) {
-        hp.asym = 1;
-        hp.shx = p->shift.ox * hp.dfx;
-        hp.shy = p->shift.oy * hp.dfy;
-        window_bins(AxisGeo(p->px), p->dx, p->shift.cx, p->shift.wx, &hp.wxlo, &hp.wxhi);
-        window_bins(AxisGeo(p->py), p->dy, p->shift.cy, p->shift.wy, &hp.wylo, &hp.wyhi);
-    }
-    if (p->type == CWO_FRESNEL_CONV || p->type == CWO_SHIFTED_FRESNEL) hp.mode = cwo::HMODE_FRESNEL;
-    else if (p->flags & CWO_FLAG_PHASE_FP32) hp.mode = cwo::HMODE_ASM_FP32;
-    else if (p->flags & CWO_FLAG_PHASE_FP64) hp.mode = cwo::HMODE_ASM_FP64;
-    else {
-        // the cheapest per-element remainder evaluation that stays within its error budget
-        int tm = 0;
-        if (zs) for (int i = 0; i < batch; ++i) tm = std::max(tm, asm_tail_mode(p->px, p->py, p->dx, p->dy, p->lambda, zs[i]));
-        else tm = asm_tail_mode(p->px, p->py, p->dx, p->dy, p->lambda, p->z);
-        hp.mode = tm == 0 ? cwo::HMODE_ASM_POLY : tm == 1 ? cwo::HMODE_ASM_EXACT : cwo::HMODE_ASM_FP64;
-    }
     // FP64 per element with per-item distances: one launch set per item, each with its own K
     const bool per_item_k = zs && hp.mode == cwo::HMODE_ASM_FP64;
 
@@ -489,6 +501,11 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     } else {
         hp.ax = p->ax; hp.ay = p->ay; hp.kf = p->kf; hp.hx = p->hx; hp.hy = p->hy;
         hp.x_item_stride = 0; hp.y_item_stride = 0; hp.kf_item_stride = 0;
+        if (p->hcache) {   // the plan's own z with the transfer function materialised
+            hp.mode = cwo::HMODE_TABLE;
+            hp.hcache = p->hcache;
+            hp.hcache_stride = p->py;
+        }
     }
 
     const long long wstride = (long long)p->ny * p->px;
@@ -746,6 +763,16 @@ cwo_status create_impl(int nx, int ny, double dx, double dy, double lambda, doub
     if ((st = dev_alloc(&p->status, 1, "status word"))) { free_plan(p); return st; }
     if ((e = cudaMemset(p->status, 0, sizeof(int))) != cudaSuccess) { free_plan(p); return cuda_fail(e, "cudaMemset"); }
     if ((st = ensure_scratch(p, 1))) { free_plan(p); return st; }
+    if ((flags & CWO_FLAG_CACHE_H) && type == CWO_ANGULAR) {
+        const int npairs = p->px / 2 + 1;
+        if ((st = dev_alloc(&p->hcache, (size_t)npairs * p->py, "transfer-function cache"))) { free_plan(p); return st; }
+        const cwo::HParams hp = base_hparams(p, nullptr, 1);
+        if ((e = cwo::launch_build_hcache(p->hcache, npairs, p->py, hp, nullptr)) != cudaSuccess ||
+            (e = cudaDeviceSynchronize()) != cudaSuccess) {
+            free_plan(p);
+            return cuda_fail(e, "building the transfer-function cache");
+        }
+    }
     *out = p;
     return CWO_OK;
 }

@@ -23,6 +23,7 @@ SHIFTED_ANGULAR = 4
 FLAG_PHASE_FP32 = 0x1
 FLAG_PHASE_FP64 = 0x2
 EPI_NONE, EPI_PHASE, EPI_AMPLITUDE, EPI_INTENSITY = 0, 1, 2, 3
+FLAG_CACHE_H = 0x8
 FLAG_LITERAL_SCALE = 0x4
 # status
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = range(6)

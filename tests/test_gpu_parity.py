@@ -248,3 +248,29 @@ def test_4096_rows_cluster_path_aligned_and_not(cwo):
     assert torch.equal(a, b)
     want = oracle.propagate(u.astype(np.complex64), 3.74e-6, 3.74e-6, 532e-9, 0.2, oracle.ANGULAR)
     assert rel(to_host(a), want) <= TOL
+
+
+@pytest.mark.parametrize("n,z,lam,pitch", [(256, 0.05, 633e-9, 10e-6), (512, -0.2, 532e-9, 4e-6), (128, 2e-4, 633e-9, 0.9e-6)])
+def test_cached_transfer_function(cwo, n, z, lam, pitch):
+    # CWO_FLAG_CACHE_H: the transfer function materialised at plan creation by the same device
+    # functions; forward, adjoint and batches equal the on-the-fly plan, and per-item distances
+    # (which cannot use the cache) still propagate correctly
+    import torch
+    u = synth.random_field(n, seed=400 + n)
+    x = to_dev(u)
+    fly = cwo.Plan(n, n, pitch, pitch, lam, z, cwo.ANGULAR)
+    cache = cwo.Plan(n, n, pitch, pitch, lam, z, cwo.ANGULAR, cwo.FLAG_CACHE_H)
+    a, b = fly.propagate(x), cache.propagate(x)
+    assert rel(to_host(b), to_host(a)) <= 1e-6
+    want = oracle.propagate(u, pitch, pitch, lam, z, oracle.ANGULAR)
+    assert rel(to_host(b), want) <= TOL
+    assert rel(to_host(cache.adjoint(x)), to_host(fly.adjoint(x))) <= 1e-6
+    xb = torch.stack([x, x * 0.5j])
+    assert rel(to_host(cache.propagate_batch(xb)), to_host(fly.propagate_batch(xb))) <= 1e-6
+    y = to_host(cache.propagate_batch(xb, z=[z / 2, 2 * z]))
+    for k, zz in enumerate((z / 2, 2 * z)):
+        w = oracle.propagate(to_host(xb[k]), pitch, pitch, lam, zz, oracle.ANGULAR)
+        assert rel(y[k], w) <= TOL
+    cache.check()
+    with pytest.raises(cwo.CwoError):
+        cwo.Plan(n, n, pitch, pitch, lam, z, cwo.FRESNEL_CONV, cwo.FLAG_CACHE_H)

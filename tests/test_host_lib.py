@@ -73,6 +73,8 @@ def test_device_bytes_is_host_only(lib, nx, ny, batch):
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 0, 3), cwo.ERR_INVALID_ARG),       # exclusive flags
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 1, 1), cwo.ERR_INVALID_ARG),       # phase flag on Fresnel
     ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 0, 4), cwo.ERR_INVALID_ARG),       # literal scale on ASM
+    ((16, 16, 1e-5, 1e-5, 633e-9, 0.1, 1, 8), cwo.ERR_INVALID_ARG),       # transfer-function cache on Fresnel
+    ((32, 32, 1e-5, 1e-5, 633e-9, 0.1, 2, 8), cwo.ERR_INVALID_ARG),       # ... and on the Fourier form
 ])
 def test_plan_create_rejects_bad_arguments_before_touching_a_device(lib, args, status):
     h = ctypes.c_void_p(123)
