@@ -37,6 +37,15 @@ cwo_status cwo_debug_twiddles(int p, float* out_ri);
  * out4: 4p floats. */
 cwo_status cwo_debug_asm_axis(int p, double pitch, double lambda, double z, int is_x, float* out4);
 
+/* The ASM transfer function H_A of Eq. ang2 on the padded px x py grid, evaluated on the host
+ * by the same per-element code and in the same mode as the column pass of an unshifted ASM plan
+ * with these parameters (px, py: padded sizes, powers of two in [32, 8192]).  Layout [iy][ix] in
+ * axis index order (frequency of index i: cwo_debug_axis_bins).  *mode_out receives the mode:
+ * 0 series tail, 1 closed-form tail, 2 per-element FP64.  out_ri: 2 px py floats,
+ * caller-owned host memory. */
+cwo_status cwo_debug_asm_h(int px, int py, double dx, double dy, double lambda, double z, int* mode_out,
+                           float* out_ri);
+
 /* Host emulation of the three CUDA passes for one [ny][nx] complex64 field (same butterflies,
  * stage positions, tables and transfer-function code, executed serially on the CPU).  type is
  * CWO_ANGULAR or CWO_FRESNEL_CONV, flags 0 or CWO_FLAG_LITERAL_SCALE, adjoint 0/1.  in_ri and

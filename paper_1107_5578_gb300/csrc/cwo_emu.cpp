@@ -159,6 +159,32 @@ extern "C" cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, do
     return CWO_OK;
 }
 
+extern "C" cwo_status cwo_debug_asm_h(int px, int py, double dx, double dy, double lambda, double z, int* mode_out,
+                                      float* out_ri) {
+    using namespace cwo;
+    using namespace cwo::host;
+    if (!mode_out || !out_ri || px < 32 || py < 32 || px > 8192 || py > 8192 || (px & (px - 1)) ||
+        (py & (py - 1)) || !(dx > 0) || !(dy > 0) || !(lambda > 0) || !std::isfinite(z))
+        return CWO_ERR_INVALID_ARG;
+    std::vector<float4> ax(px), ay(py);
+    float K = 0.f;
+    make_h_tables(px, py, dx, dy, lambda, z, false, false, ax.data(), ay.data(), nullptr, nullptr, &K);
+    const int tmode = asm_tail_mode(px, py, dx, dy, lambda, z);
+    const std::vector<int> kbx = bin_table(AxisGeo(px)), kby = bin_table(AxisGeo(py));
+    const double sx = lambda * lambda / ((double)px * dx * (double)px * dx);
+    const double sy = lambda * lambda / ((double)py * dy * (double)py * dy);
+    float2* out = (float2*)out_ri;
+    for (int i = 0; i < py; ++i)
+        for (int c = 0; c < px; ++c) {
+            float2 h;
+            if (tmode == 2) h = asm_h_fp64(kbx[c], kby[i], z / lambda, sx, sy);
+            else h = tmode == 0 ? asm_h_reduced<true>(ax[c], ay[i], K) : asm_h_reduced<false>(ax[c], ay[i], K);
+            out[(size_t)i * px + c] = h;
+        }
+    *mode_out = tmode;
+    return CWO_OK;
+}
+
 extern "C" cwo_status cwo_debug_line_fft(int p, int inverse, const float* in_ri, float* out_ri) {
     using namespace cwo;
     using namespace cwo::host;

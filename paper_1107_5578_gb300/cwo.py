@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
                 "cwo_debug_asm_axis": ([i, d, d, d, i, vp], i),
                 "cwo_debug_emulate": ([i, i, d, d, d, d, i, u, i, vp, vp], i),
                 "cwo_debug_line_fft": ([i, i, vp, vp], i),
+                "cwo_debug_asm_h": ([i, i, d, d, d, d, ctypes.POINTER(ctypes.c_int), vp], i),
                 "cwo_debug_bounded_wait": ([u, i, ctypes.POINTER(ctypes.c_int)], i),
             }
             for name, (args, res) in sig.items():
@@ -371,6 +372,17 @@ def emulate(u, dx, dy, wavelength, z, kind=ANGULAR, flags=0, adjoint=False):
     check(lib().cwo_debug_emulate(nx, ny, dx, dy, wavelength, z, kind, flags, int(adjoint),
                                   a.ctypes.data, out.ctypes.data), "cwo_debug_emulate")
     return out
+
+
+def asm_h(px, py, dx, dy, wavelength, z):
+    """Host evaluation of the ASM transfer function in the column pass's own mode (test
+    support): (mode, complex64 [py][px] in axis index order)."""
+    import numpy as np
+    out = np.empty((py, px), dtype=np.complex64)
+    mode = ctypes.c_int(99)
+    check(lib().cwo_debug_asm_h(px, py, dx, dy, wavelength, z, ctypes.byref(mode), out.ctypes.data),
+          "cwo_debug_asm_h")
+    return mode.value, out
 
 
 def line_fft(x, inverse=False):

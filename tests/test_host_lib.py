@@ -189,3 +189,28 @@ def test_shifted_plan_argument_checks_need_no_device(lib):
     assert e.value.status == cwo.ERR_UNSUPPORTED
     with pytest.raises(cwo.CwoError):
         cwo.Plan(64, 64, 8e-6, 8e-6, 532e-9, 0.01, kind=cwo.SHIFTED_ANGULAR)   # needs the shifted constructor
+
+
+@pytest.mark.parametrize("px,py,dx,lam,z,mode,tol", [
+    (4096, 512, 10e-6, 633e-9, 0.05, 0, 1e-6),      # 2048^2 field geometry
+    (1024, 1024, 10e-6, 633e-9, -0.1, 0, 1e-6),
+    (2048, 256, 3.74e-6, 532e-9, 1.0, 0, 1e-6),     # cross term up to ~12 cycles: float-float
+    (512, 512, 0.5e-6, 633e-9, 20e-6, 1, 4e-6),     # s up to 0.8: closed-form tail
+    (256, 256, 0.4e-6, 633e-9, 0.01, 2, 1e-7),      # K s^3 large: per-element FP64, evanescent corners
+])
+def test_asm_transfer_function_phase_against_fp64(lib, px, py, dx, lam, z, mode, tol):
+    # H_A = exp(2 pi i (z / lambda) sqrt(1 - lambda^2 (fx^2 + fy^2))), zero where the root is
+    # imaginary (Eq. ang2), evaluated directly in FP64 on the padded frequency grid
+    got_mode, h = cwo.asm_h(px, py, dx, dx, lam, z)
+    assert got_mode == mode
+    kx, ky = cwo.axis_bins(px).astype(np.int64), cwo.axis_bins(py).astype(np.int64)
+    kx = np.where(kx < px // 2, kx, kx - px)
+    ky = np.where(ky < py // 2, ky, ky - py)
+    s = lam ** 2 * ((kx[None, :] / (px * dx)) ** 2 + (ky[:, None] / (py * dx)) ** 2)
+    prop = s < 1.0 - 1e-6
+    psi = (z / lam) * np.sqrt(np.where(prop, 1.0 - s, 0.0))
+    ref = np.exp(2j * np.pi * (psi - np.round(psi)))
+    err = np.angle(h[prop] * np.conj(ref[prop])) / (2 * np.pi)
+    assert np.max(np.abs(err)) < tol, np.max(np.abs(err))
+    assert np.max(np.abs(np.abs(h[prop]) - 1.0)) < 1e-6
+    assert np.all(h[s > 1.0 + 1e-6] == 0)
