@@ -39,7 +39,7 @@ COL_BYTES_PER_PROP = 32 * N * N      # column pass: read + write the Ny x Px int
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the column pass at
 # batch 16, from one ncu capture of the current kernel; scaled by the batch (traffic grows in
 # proportion to the fields processed)
-NCU_TRAFFIC_B16 = {"col_fwd_h_inv": 2083.8e6}
+NCU_TRAFFIC_B16 = {"col_fwd_h_inv": 2084.26e6}
 
 
 def traffic_bytes(kernel, batch):
@@ -76,6 +76,15 @@ class ClockSampler:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # wait (at most 3 s) for the first sample; only samples taken after it are summarised
+        self.skip = 0
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < 3.0:
+            with open(self.path) as f:
+                self.skip = sum(1 for _ in f)
+            if self.skip:
+                break
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *a):
@@ -100,6 +109,8 @@ class ClockSampler:
                 os.unlink(self.path)
             except Exception:
                 pass
+        if len(rows) > self.skip:
+            rows = rows[self.skip:]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -227,6 +238,35 @@ def serving_measurement(dev, n_req, rate_hz):
             "continuous": cont, "serial": ser}
 
 
+def timed_steps(plan, x, y, steps, stream, before=None):
+    """Run `steps` propagations of the batch x back to back on `stream`; return the event time of
+    the whole run (ms) and the summed per-pass times (ms), read after the run from one set of
+    pass events per step (recorded by the library on the launching stream)."""
+    import torch
+    step_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for evs in step_ev:
+        for e_ in evs:
+            e_.record(stream)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if before is not None:
+        before()
+    t0.record(stream)
+    for i in range(steps):
+        plan.set_timing_events(step_ev[i])
+        plan.propagate_batch(x, out=y)
+    t1.record(stream)
+    return t0, t1, step_ev
+
+
+def pass_sums(plan, step_ev):
+    plan.set_timing_events(None)
+    pp = np.zeros(3)
+    for evs in step_ev:
+        pp += [evs[0].elapsed_time(evs[1]), evs[1].elapsed_time(evs[2]), evs[2].elapsed_time(evs[3])]
+    return pp
+
+
 def once_h_measurement(x, y, steps):
     """The same 2048^2 ASM batch with the transfer function materialised at plan creation
     (CWO_FLAG_CACHE_H, the paper's "once-calculation"): propagations/s and per-pass times."""
@@ -237,19 +277,9 @@ def once_h_measurement(x, y, steps):
     plan.reserve(B)
     for _ in range(3):
         plan.propagate_batch(x, out=y)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    plan.set_timing_events(ev)
-    pp = np.zeros(3)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a, b, step_ev = timed_steps(plan, x, y, steps, torch.cuda.current_stream())
     torch.cuda.synchronize()
-    a.record()
-    for _ in range(steps):
-        plan.propagate_batch(x, out=y)
-        ev[3].synchronize()
-        pp += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
-    b.record()
-    torch.cuda.synchronize()
-    plan.set_timing_events(None)
+    pp = pass_sums(plan, step_ev)
     ms = a.elapsed_time(b) / steps
     plan.close()
     return {"workload": "asm_2048_pad4096, transfer function cached per plan", "value": round(B / (ms / 1e3), 2),
@@ -290,7 +320,8 @@ def gs_measurement(dev, iterations=40):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 500 for this implementation, 20 for the reference arm)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -299,6 +330,8 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=2000.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else 500
     world, rank, local = dist_setup()
 
     if args.impl == "reference":
@@ -325,7 +358,6 @@ def main():
     y = torch.empty_like(x)
     host_out = torch.empty((B, N, N), dtype=torch.complex64).pin_memory()
     stream = torch.cuda.current_stream()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
     def barrier():
         if world > 1:
@@ -336,23 +368,18 @@ def main():
     for _ in range(args.warmup):
         plan.propagate_batch(x, out=y)
     barrier()
-    plan.set_timing_events(ev)
-    per_pass = np.zeros(3)
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    wall = {}
+
+    def start():
         barrier()
-        t_start.record(stream)
-        wall0 = time.perf_counter()
-        for _ in range(args.steps):
-            plan.propagate_batch(x, out=y)
-            # per-pass durations of this step (events recorded by the library on this stream)
-            ev[3].synchronize()
-            per_pass += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
-        t_end.record(stream)
+        wall["t0"] = time.perf_counter()
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_start, t_end, step_ev = timed_steps(plan, x, y, args.steps, stream, before=start)
         barrier()
         wall1 = time.perf_counter()
-    plan.set_timing_events(None)
+    wall0 = wall["t0"]
+    per_pass = pass_sums(plan, step_ev)
     clocks = clk.summary()
     ms_total = replicas.max_over_ranks(t_start.elapsed_time(t_end), dev)
     ms_step = ms_total / args.steps
