@@ -274,3 +274,32 @@ def test_cached_transfer_function(cwo, n, z, lam, pitch):
     cache.check()
     with pytest.raises(cwo.CwoError):
         cwo.Plan(n, n, pitch, pitch, lam, z, cwo.FRESNEL_CONV, cwo.FLAG_CACHE_H)
+
+
+# ------------------------------------------------- properties at full size (no oracle output)
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kind,z", [(0, 0.05), (1, 0.2)])
+def test_adjoint_dot_product_2048(cwo, kind, z):
+    # <A x, y> = <x, A^H y> for the cropped linear operator A of one plan (its adjoint conjugates
+    # H and C); bounded by 1e-6 of ||A x|| ||y||, the Cauchy-Schwarz scale of either side
+    n = 2048
+    x = synth.random_field(n, seed=61)
+    y = synth.random_field(n, seed=62)
+    plan = cwo.Plan(n, n, 10e-6, 10e-6, 633e-9, z, kind)
+    ax = to_host(plan.propagate(to_dev(x)))
+    ahy = to_host(plan.adjoint(to_dev(y)))
+    plan.check()
+    plan.close()
+    lhs = np.vdot(y, ax)
+    rhs = np.vdot(ahy, x)
+    assert abs(lhs - rhs) <= 1e-6 * np.linalg.norm(ax) * np.linalg.norm(y)
+
+
+@pytest.mark.slow
+def test_asm_zero_distance_identity_4096(cwo):
+    # H = 1 at z = 0: the largest field comes back through both padded transforms unchanged
+    n = 4096
+    u = synth.random_field(n, seed=63)
+    got = gpu_prop(cwo, u, 3.74e-6, 3.74e-6, 532e-9, 0.0, 0)
+    assert rel(got, u) <= 2e-6
