@@ -287,6 +287,29 @@ def once_h_measurement(x, y, steps):
             "cache_bytes": (N + 1) * 2 * N * 8}
 
 
+def fresnel_batch_measurement(x, y, steps, hbm_peak):
+    """Fresnel diffraction (convolution form) of the same 16 fields of 2048^2 (532 nm, 8 um,
+    z = 0.2 m): two separable line passes, 32 N^2 algorithmic bytes per propagation."""
+    import torch
+    from paper_1107_5578_gb300 import cwo
+    B = x.shape[0]
+    plan = cwo.Plan(N, N, 8e-6, 8e-6, 532e-9, 0.2, cwo.FRESNEL_CONV)
+    plan.reserve(B)
+    for _ in range(3):
+        plan.propagate_batch(x, out=y)
+    a, b, step_ev = timed_steps(plan, x, y, steps, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    pp = pass_sums(plan, step_ev) / steps
+    ms = a.elapsed_time(b) / steps
+    launches = plan.launches_per_call
+    plan.close()
+    gbs = 32 * N * N * B / (ms / 1e3) / 1e9
+    return {"workload": "fresnel_conv_2048_pad4096_batch16", "value": round(B / (ms / 1e3), 2), "unit": UNIT,
+            "passes_ms": {"line_x": round(pp[0], 4), "line_y": round(pp[1], 4)},
+            "hbm_gbs_algorithmic": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm_peak, 4),
+            "bytes_per_prop": 32 * N * N, "launches_per_call": launches}
+
+
 # Table "Calculation times of the GS algorithm on the CPU and GPUs", 40 iterations, GeForce GTX580
 GS_PAPER_MS_40 = {512: 338.0, 1024: 1.19e3, 2048: 4.65e3}
 
@@ -429,6 +452,7 @@ def main():
 
     stack = stack_measurement(dev, peaks()[0])
     once_h = once_h_measurement(x, y, args.steps) if rank == 0 else None
+    fresnel_b = fresnel_batch_measurement(x, y, args.steps, peaks()[0]) if rank == 0 else None
     gs_res = gs_measurement(dev) if rank == 0 else None
     serve = serving_measurement(dev, args.serving_requests, args.serving_rate) \
         if args.serving_requests > 0 and rank == 0 else None
@@ -464,6 +488,7 @@ def main():
         "gpu_launches": plan.launches_per_call * args.steps,
         "fresnel_stack": stack,
         "asm_once_h": once_h,
+        "fresnel_batch": fresnel_b,
         "gs_kinoform": gs_res,
         "serving": serve,
         "serving_4x_rate": serve_high,

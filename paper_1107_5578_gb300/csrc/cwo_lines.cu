@@ -1,0 +1,218 @@
+// cwo_lines.cu -- Fresnel diffraction in the convolution form as two separable line passes.
+//
+// The sampled Fresnel impulse response of Eq. fre_conv_prop_d is a product of one chirp per axis,
+// h_F(x, y) = exp(i pi x^2 / (lambda z)) exp(i pi y^2 / (lambda z)), and the zero-padded FFT method
+// of Eq. fre_conv_fft equals the linear convolution of the field with it.  That 2-D convolution
+// is exactly a 1-D linear convolution of every row with the x chirp followed by one of every column
+// with the y chirp, and each 1-D convolution is again the padded FFT method on a line:
+//   expand the line to P = 2N, FFT, multiply by the axis transfer function (the FP64 DFT of the
+//   sampled chirp; the x table carries the coefficient C), IFFT, keep the first N samples.
+// One kernel does both passes.  Pass 1 takes the Ny rows of the field and stores its results
+// transposed into a column-major N x N intermediate; pass 2 takes the Nx contiguous columns of
+// that intermediate and stores transposed again, i.e. into the row-major output.  Each pass reads
+// and writes 8 N^2 bytes (32 N^2 per propagation against 80 N^2 for the three-pass method with an
+// N x 2N intermediate) and transforms half as many lines of length 2N as the column pass.
+//
+// A CTA holds R lines (lanes row-fastest, as in the row passes), loads each thread's 8 nonzero
+// stage-0 samples directly, runs the forward DIF stages, multiplies by the table in DIF order
+// (register e of thread t holds the frequency of axis index e T + t), runs the adjoint stages back
+// to natural order, scales, and writes the kept half as a dense tile [position][line] that TMA
+// stores as boxes of R lines x min(256, N) positions.
+#include <algorithm>
+#include <stdint.h>
+
+#include "cwo_fft.cuh"
+#include "cwo_internal.h"
+#include "cwo_launch.cuh"
+#include "cwo_tma.cuh"
+
+namespace cwo {
+
+// lines per CTA: 4 (one 32-byte sector per stored position) while the exchange space fits, 2 at
+// P = 8192
+template <int P> constexpr int line_rows() { return P >= 8192 ? 2 : (P >= 256 ? 4 : 8); }
+
+template <int P, int R>
+__host__ __device__ constexpr size_t line_smem_words() {
+    return PadLayout<P, R>::WORDS > (size_t)R * (P / 2) ? PadLayout<P, R>::WORDS : (size_t)R * (P / 2);
+}
+
+template <int P, int R>
+__global__ void __launch_bounds__(R * (P / 16))
+k_line_conv(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap omap,
+            const float2* __restrict__ h, long long h_item_stride, int conj, float scale,
+            const float4* __restrict__ tw) {
+    pdl_wait();
+    constexpr int T = P / 16, N = P / 2, NT = R * T;
+    constexpr int BOX = N < kTmaBoxCols ? N : kTmaBoxCols;
+    extern __shared__ __align__(1024) float2 sm[];
+    const int r = threadIdx.x % R, t = threadIdx.x / R;
+    const int l0 = blockIdx.x * R;
+    const int item = blockIdx.y;
+    const float2* src = in + item * in_item_stride + (long long)(l0 + r) * N;
+    float2 v[16];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = __ldg(src + t + e * T);   // stage-0 positions t + e P/16 < N
+#pragma unroll
+    for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);   // the expanded half, never loaded
+    const TwTable<P> twt{tw, t};
+    fwd_from<P, R, PadLayout<P, R>, 0, 8, 0>(v, sm, r, t, twt);
+    const float2* hh = h + item * h_item_stride + t;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const float2 w = __ldg(hh + e * T);
+        v[e] = conj ? cmulc(v[e], w) : cmul(v[e], w);
+    }
+    inv_from<P, R, PadLayout<P, R>, Geo<P>::NST - 1, 0, 0>(v, sm, r, t, twt);
+    // kept positions t + e T (e < 8): tile index (t + e T) R + r = e R T + threadIdx.x; the
+    // exchange region is free after the trailing barrier of the last exchange
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sm[e * NT + threadIdx.x] = cscale(v[e], scale);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll 1
+        for (int b = 0; b < N / BOX; ++b) tma_store_3d(&omap, sm + b * BOX * R, l0, b * BOX, item);
+        tma_store_commit_and_drain();
+    }
+}
+
+// Persistent form: each CTA walks groups g = blockIdx.x, + gridDim.x, ... of R lines, each thread
+// transforming a pair of lines (c0 = 2 cp and c0 + 1; the pair shares its twiddle and
+// transfer-function loads: every line of an item has the same axis table).  The lines of the next
+// group are copied into a staging buffer by the bulk-copy engine (one copy per line, completion
+// on an mbarrier, bounded wait) while the current group is transformed; the first stage runs in
+// registers while the previous group's tile (which aliases the exchange region) drains through
+// its TMA stores.  Needs every line on a 16-byte boundary.
+template <int P>
+__host__ __device__ constexpr int line_stage_stride() { return P / 2 + 4; }
+
+template <int P, int R>
+__host__ __device__ constexpr size_t line_p_smem_bytes() {
+    return (line_smem_words<P, R>() + (size_t)R * line_stage_stride<P>()) * sizeof(float2) + sizeof(uint64_t);
+}
+
+template <int P, int R>
+__global__ void __launch_bounds__((R / 2) * (P / 16), (R / 2) * (P / 16) >= 512 ? 1 : 2)
+k_line_conv_p(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap omap,
+              const float2* __restrict__ h, long long h_item_stride, int conj, float scale,
+              const float4* __restrict__ tw, int groups_per_item, int total_groups, int* status) {
+    pdl_wait();
+    constexpr int T = P / 16, N = P / 2, SST = line_stage_stride<P>();
+    constexpr int BOX = N < kTmaBoxCols ? N : kTmaBoxCols;
+    using Lay = PadLayout<P, R>;
+    extern __shared__ __align__(1024) float2 sm[];
+    float2* stage = sm + line_smem_words<P, R>();
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(stage + R * SST);
+    const int t = threadIdx.x % T, c0 = 2 * (threadIdx.x / T);
+    auto issue = [&](int g) {   // thread 0: the R lines of group g into the staging buffer
+        const int item = g / groups_per_item, l0 = (g % groups_per_item) * R;
+        const float2* src = in + item * in_item_stride + (long long)l0 * N;
+        mbar_arrive_expect_tx(mbar, (unsigned)(R * N * sizeof(float2)));
+#pragma unroll 1
+        for (int rr = 0; rr < R; ++rr) bulk_load(stage + rr * SST, src + rr * N, (unsigned)(N * sizeof(float2)), mbar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        if ((int)blockIdx.x < total_groups) issue(blockIdx.x);
+    }
+    __syncthreads();
+    unsigned parity = 0;
+#pragma unroll 1
+    for (int g = blockIdx.x; g < total_groups; g += gridDim.x, parity ^= 1u) {
+        const bool ok = mbar_wait_bounded(mbar, parity, status);
+        float2 a[16], b[16];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {   // stage-0 positions t + e P/16 of lines c0 and c0 + 1
+            a[e] = stage[c0 * SST + t + e * T];
+            b[e] = stage[(c0 + 1) * SST + t + e * T];
+        }
+#pragma unroll
+        for (int e = 8; e < 16; ++e) { a[e] = make_float2(0.f, 0.f); b[e] = make_float2(0.f, 0.f); }
+        fence_proxy_async_smem();   // these reads of the staging buffer precede the next bulk copy into it
+        if (__syncthreads_or(!ok)) break;                                // a copy did not land
+        if (threadIdx.x == 0 && g + (int)gridDim.x < total_groups) issue(g + gridDim.x);
+        stage_butterflies<P, 0, false, 8>(a);
+        stage_butterflies<P, 0, false, 8>(b);
+        if constexpr (Geo<P>::NST > 1) twiddle2<P, 0, false>(a, b, tw, t);
+        if (threadIdx.x == 0) tma_store_wait_read();                      // previous tile read out
+        __syncthreads();
+        if constexpr (Geo<P>::NST > 1) {
+            exchange2<P, R, Lay, 0, 1, 0, 0>(sm, c0, t, a, b);
+            fwd2_from<P, R, Lay, 1, 8, 0>(a, b, sm, c0, t, tw);
+        }
+        {
+            const float2* hh = h + (g / groups_per_item) * h_item_stride + t;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float2 w = __ldg(hh + e * T);
+                a[e] = conj ? cmulc(a[e], w) : cmul(a[e], w);
+                b[e] = conj ? cmulc(b[e], w) : cmul(b[e], w);
+            }
+        }
+        inv2_from<P, R, Lay, Geo<P>::NST - 1, 0, 0>(a, b, sm, c0, t, tw);
+        // kept positions t + e T (e < 8) of lines c0, c0 + 1: tile words (t + e T) R + c0, + 1
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float2 x = cscale(a[e], scale), y = cscale(b[e], scale);
+            *reinterpret_cast<float4*>(sm + (t + e * T) * R + c0) = make_float4(x.x, x.y, y.x, y.y);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int item = g / groups_per_item, l0 = (g % groups_per_item) * R;
+#pragma unroll 1
+            for (int bx = 0; bx < N / BOX; ++bx) tma_store_3d(&omap, sm + bx * BOX * R, l0, bx * BOX, item);
+            tma_store_commit();
+        }
+    }
+    if (threadIdx.x == 0) tma_store_wait_read();
+}
+
+template <int P>
+static cudaError_t line_conv_impl(const float2* in, long long in_item_stride, const CUtensorMap* omap, int lines,
+                                  int items, const float2* h, long long h_item_stride, int conj, float scale,
+                                  const float4* tw, int* status, cudaStream_t st) {
+    constexpr int R = line_rows<P>();
+    constexpr int T = P / 16;
+    if (lines % R || items < 1 || items > 65535) return cudaErrorInvalidValue;
+    const bool aligned = ((uintptr_t)in % 16 == 0) && (in_item_stride % 2 == 0);
+    if (P >= 512 && aligned && status) {
+        const size_t smem = line_p_smem_bytes<P, R>();
+        int resident = 0;
+        cudaError_t e = kernel_setup<k_line_conv_p<P, R>>(smem, (R / 2) * T, &resident);
+        if (e != cudaSuccess) return e;
+        const int groups = (lines / R) * items;
+        const int grid = std::min(groups, resident);
+        if (grid > 0)
+            return pdl_launch(k_line_conv_p<P, R>, dim3(grid), dim3((R / 2) * T), smem, st, in, in_item_stride, *omap,
+                              h, h_item_stride, conj, scale, tw, lines / R, groups, status);
+    }
+    const size_t smem = line_smem_words<P, R>() * sizeof(float2);
+    cudaError_t e = kernel_setup<k_line_conv<P, R>>(smem, R * T, nullptr);
+    if (e != cudaSuccess) return e;
+    return pdl_launch(k_line_conv<P, R>, dim3(lines / R, items), dim3(R * T), smem, st, in, in_item_stride, *omap, h,
+                      h_item_stride, conj, scale, tw);
+}
+
+int line_block_rows(int p) {
+    switch (p) {
+#define CASE(P) case P: return line_rows<P>();
+        CASE(32) CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024) CASE(2048) CASE(4096) CASE(8192)
+#undef CASE
+        default: return 0;
+    }
+}
+
+cudaError_t launch_line_conv(int p, const float2* in, long long in_item_stride, const CUtensorMap* omap, int lines,
+                             int items, const float2* h, long long h_item_stride, int conj, float scale,
+                             const float4* tw, int* status, cudaStream_t st) {
+    switch (p) {
+#define CASE(P) case P: return line_conv_impl<P>(in, in_item_stride, omap, lines, items, h, h_item_stride, conj, scale, tw, status, st);
+        CASE(32) CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024) CASE(2048) CASE(4096) CASE(8192)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace cwo

@@ -178,6 +178,8 @@ struct cwo_plan {
     cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
     CUtensorMap wmap_f;        // TMA maps of the scratch intermediate [scap][px][ny] for the
     CUtensorMap wmap_i;        // forward and inverse row passes (different box heights)
+    CUtensorMap wmap_s;        // Fresnel convolution form: the [scap][nx][ny] intermediate of its
+                               // separable line passes
     int* status = nullptr;     // device status word: bounded waits that expired (cwo_plan_check)
     // shifted angular spectrum (CWO_SHIFTED_ANGULAR): shift and Rect windows (Eq. shift_ang1)
     bool shifted = false;
@@ -266,7 +268,9 @@ cwo_status ensure_scratch(cwo_plan* p, int items) {
     cwo_status st = dev_alloc(&p->scratch, (size_t)items * p->ny * p->px, "scratch");
     if (st != CWO_OK) return st;
     if ((e = cwo::make_intermediate_map(&p->wmap_f, p->scratch, p->ny, p->px, items, cwo::row_block_rows(p->px, false))) ||
-        (e = cwo::make_intermediate_map(&p->wmap_i, p->scratch, p->ny, p->px, items, cwo::row_block_rows(p->px, true))))
+        (e = cwo::make_intermediate_map(&p->wmap_i, p->scratch, p->ny, p->px, items, cwo::row_block_rows(p->px, true))) ||
+        (p->type == CWO_FRESNEL_CONV &&
+         (e = cwo::make_intermediate_map(&p->wmap_s, p->scratch, p->ny, p->nx, items, cwo::line_block_rows(p->px)))))
         return cuda_fail(e, "tensor map of the intermediate");
     p->scap = items;
     return CWO_OK;
@@ -524,6 +528,23 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     float2* fout = (float2*)out;
     cudaError_t e;
     const float scale = (float)(1.0 / ((double)p->px * (double)p->py));
+    if (p->type == CWO_FRESNEL_CONV && !stack && ep.mode == cwo::EPI_NONE && (uintptr_t)out % 16 == 0) {
+        // separable form: a padded line convolution along x into the column-major Nx x Ny
+        // intermediate, then one along y into the output (cwo_lines.cu)
+        CUtensorMap omap;
+        if ((e = cwo::make_intermediate_map(&omap, out, p->nx, p->ny, batch, cwo::line_block_rows(p->py))))
+            return cuda_fail(e, "tensor map of the output");
+        const long long istr = in_stride ? in_stride : field;
+        if ((e = mark(0)) ||
+            (e = cwo::launch_line_conv(p->px, fin, istr, &p->wmap_s, p->ny, batch, hp.hx, hp.x_item_stride, hp.conj,
+                                       (float)(1.0 / p->px), p->tw_x, p->status, s)) ||
+            (e = mark(1)) ||
+            (e = cwo::launch_line_conv(p->py, p->scratch, field, &omap, p->nx, batch, hp.hy, hp.y_item_stride, hp.conj,
+                                       (float)(1.0 / p->py), p->tw_y, p->status, s)) ||
+            (e = mark(2)) || (e = mark(3)))
+            return cuda_fail(e, "separable Fresnel launch");
+        return CWO_OK;
+    }
     if (stack) {
         // the shared source: row pass once, then per-plane column and inverse row passes
         float2* w0 = p->scratch;
@@ -936,7 +957,10 @@ cwo_status cwo_gs_run(cwo_plan* plan, const float* amplitude, void* field_c64, f
     return st;
 }
 
-int cwo_launches_per_call(const cwo_plan* plan) { return plan ? (plan->type == CWO_FRESNEL_FOURIER ? 2 : 3) : 0; }
+int cwo_launches_per_call(const cwo_plan* plan) {
+    if (!plan) return 0;
+    return plan->type == CWO_FRESNEL_FOURIER || plan->type == CWO_FRESNEL_CONV ? 2 : 3;
+}
 
 cwo_status cwo_plan_check(cwo_plan* plan) {
     if (!plan) return fail(CWO_ERR_INVALID_ARG, "plan is NULL");

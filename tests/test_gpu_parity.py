@@ -303,3 +303,55 @@ def test_asm_zero_distance_identity_4096(cwo):
     u = synth.random_field(n, seed=63)
     got = gpu_prop(cwo, u, 3.74e-6, 3.74e-6, 532e-9, 0.0, 0)
     assert rel(got, u) <= 2e-6
+
+
+@pytest.mark.parametrize("nx,ny,adjoint", [(256, 256, False), (512, 64, True), (32, 1024, False), (1024, 32, True)])
+def test_fresnel_separable_equals_three_pass(cwo, nx, ny, adjoint):
+    # the convolution-form Fresnel plan runs two separable line passes; an output that does not
+    # start on a 16-byte boundary takes the three-pass method: both agree with each other and the
+    # oracle
+    import torch
+    u = synth.random_field(nx, seed=70 + nx, ny=ny)
+    plan = cwo.Plan(nx, ny, 8e-6, 6e-6, 532e-9, 0.04, cwo.FRESNEL_CONV)
+    assert plan.launches_per_call == 2
+    x = to_dev(u)
+    run = plan.adjoint if adjoint else plan.propagate
+    a = to_host(run(x))
+    buf = torch.empty(nx * ny + 1, dtype=torch.complex64, device="cuda")
+    out = buf[1:].view(ny, nx)
+    assert out.data_ptr() % 16 == 8
+    run(x, out=out)
+    b = to_host(out)
+    # an input off a 16-byte boundary: the first line pass loads per thread (no bulk copies)
+    ibuf = torch.empty(nx * ny + 1, dtype=torch.complex64, device="cuda")
+    xm = ibuf[1:].view(ny, nx)
+    xm.copy_(x)
+    c = to_host(run(xm))
+    plan.check()
+    plan.close()
+    want = oracle.propagate(u, 8e-6, 6e-6, 532e-9, 0.04, oracle.FRESNEL_CONV, oracle.ADJOINT if adjoint else 0)
+    assert rel(a, want) <= TOL and rel(b, want) <= TOL
+    assert rel(a, b) <= 1e-5
+    assert np.array_equal(a, c)
+
+
+@pytest.mark.slow
+def test_fresnel_4096_and_batch16_2048(cwo):
+    # the largest field (lines padded to 8192: two lines per CTA) and a 16-field batch as the
+    # serving and stack workloads size it; sampled items against the oracle
+    import torch
+    u = synth.random_field(4096, seed=71)
+    plan = cwo.Plan(4096, 4096, 3.74e-6, 3.74e-6, 532e-9, 0.3, cwo.FRESNEL_CONV)
+    got = to_host(plan.propagate(to_dev(u)))
+    plan.close()
+    assert rel(got, oracle.propagate(u, 3.74e-6, 3.74e-6, 532e-9, 0.3, oracle.FRESNEL_CONV)) <= TOL
+    n, b = 2048, 16
+    base = synth.random_field(n, seed=72)
+    zs = list(np.linspace(0.1, 0.4, b))
+    x = to_dev(np.broadcast_to(base, (b, n, n)))
+    plan = cwo.Plan(n, n, 8e-6, 8e-6, 532e-9, 0.2, cwo.FRESNEL_CONV)
+    y = to_host(plan.propagate_batch(x, z=zs))
+    plan.check()
+    plan.close()
+    for k in (0, 9):
+        assert rel(y[k], oracle.propagate(base, 8e-6, 8e-6, 532e-9, zs[k], oracle.FRESNEL_CONV)) <= TOL
