@@ -28,9 +28,10 @@
 
 namespace cwo {
 
-// lines per CTA: 4 (one 32-byte sector per stored position) while the exchange space fits, 2 at
-// P = 8192
-template <int P> constexpr int line_rows() { return P >= 8192 ? 2 : (P >= 256 ? 4 : 8); }
+// lines per group: 2 from P = 4096 (one pair per thread: two 256-thread CTAs per SM at P = 4096,
+// measured 73 against 79 us per 2048^2 field with 4-line groups and their whole-sector column
+// pieces), 4 below
+template <int P> constexpr int line_rows() { return P >= 4096 ? 2 : (P >= 256 ? 4 : 8); }
 
 template <int P, int R>
 __host__ __device__ constexpr size_t line_smem_words() {
