@@ -156,7 +156,8 @@ __host__ __device__ constexpr size_t row_fwd_p_smem_bytes() {
 }
 
 template <int P, int R, bool PRE>
-__global__ void __launch_bounds__(R * (P / 16), 1)
+// two CTAs per SM where a CTA has fewer than 1024 threads (1024^2 fields: 5.8 -> 5.3 us per field)
+__global__ void __launch_bounds__(R * (P / 16), R * (P / 16) >= 1024 ? 1 : 2)
 k_row_fwd_p(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap wmap,
             int item_off, int groups_per_item, int total_groups, const float4* __restrict__ tw, int* status,
             const Prefactor pre) {
