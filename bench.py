@@ -39,7 +39,7 @@ COL_BYTES_PER_PROP = 32 * N * N      # column pass: read + write the Ny x Px int
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the column pass at
 # batch 16, from one ncu capture of the current kernel; scaled by the batch (traffic grows in
 # proportion to the fields processed)
-NCU_TRAFFIC_B16 = {"col_fwd_h_inv": 2084.26e6}
+NCU_TRAFFIC_B16 = {"col_fwd_h_inv": 2084.01e6}
 
 
 def traffic_bytes(kernel, batch):
