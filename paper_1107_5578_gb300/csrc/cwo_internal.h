@@ -106,13 +106,14 @@ cudaError_t launch_build_hcache(float2* out, int npairs, int py, const HParams& 
 // Fresnel diffraction in Fourier form (cwo_fourier.cu): source chirp + row FFT into the
 // [items][Px = Nx][Ny] intermediate; column FFT + destination chirp into the centred output
 // separable Fresnel line pass (cwo_lines.cu): `lines` lines of P/2 contiguous samples per item,
-// expanded to P, convolved through the axis table h (DIF order, P entries per item), scaled and
-// stored transposed through omap (dims: lines, P/2 positions, items; boxes of
-// line_block_rows(P) lines)
+// optionally multiplied by pre[position], expanded to P, convolved through the axis table h (DIF
+// order, P entries per item), scaled, optionally multiplied by post[position], and stored
+// transposed through omap (dims: lines, P/2 positions, items; boxes of line_block_rows(P) lines).
+// pre and post: both or neither.
 int line_block_rows(int p);
 cudaError_t launch_line_conv(int p, const float2* in, long long in_item_stride, const CUtensorMap* omap, int lines,
                              int items, const float2* h, long long h_item_stride, int conj, float scale,
-                             const float4* tw, int* status, cudaStream_t st);
+                             const float4* tw, int* status, const float2* pre, const float2* post, cudaStream_t st);
 cudaError_t launch_fourier_rows(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap, int ny,
                                 int items, const float2* pre_x, const float2* pre_y, const float4* tw, cudaStream_t st);
 cudaError_t launch_fourier_cols(int py, const float2* win, long long win_item_stride, float2* out, long long out_item_stride,

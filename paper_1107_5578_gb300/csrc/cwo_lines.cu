@@ -13,6 +13,10 @@
 // and writes 8 N^2 bytes (32 N^2 per propagation against 80 N^2 for the three-pass method with an
 // N x 2N intermediate) and transforms half as many lines of length 2N as the column pass.
 //
+// The shifted Fresnel diffraction (Eqs. shift_fre1 - shift_fre3) is the same convolution between a
+// source factor f and a destination factor q, both products of one factor per axis, so each pass
+// also multiplies its input samples by f along its axis and its kept outputs by q (FAC).
+//
 // A CTA holds R lines (lanes row-fastest, as in the row passes), loads each thread's 8 nonzero
 // stage-0 samples directly, runs the forward DIF stages, multiplies by the table in DIF order
 // (register e of thread t holds the frequency of axis index e T + t), runs the adjoint stages back
@@ -38,11 +42,11 @@ __host__ __device__ constexpr size_t line_smem_words() {
     return PadLayout<P, R>::WORDS > (size_t)R * (P / 2) ? PadLayout<P, R>::WORDS : (size_t)R * (P / 2);
 }
 
-template <int P, int R>
+template <int P, int R, bool FAC>
 __global__ void __launch_bounds__(R * (P / 16))
 k_line_conv(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap omap,
             const float2* __restrict__ h, long long h_item_stride, int conj, float scale,
-            const float4* __restrict__ tw) {
+            const float4* __restrict__ tw, const float2* __restrict__ pre, const float2* __restrict__ post) {
     pdl_wait();
     constexpr int T = P / 16, N = P / 2, NT = R * T;
     constexpr int BOX = N < kTmaBoxCols ? N : kTmaBoxCols;
@@ -56,6 +60,10 @@ k_line_conv(const float2* __restrict__ in, long long in_item_stride, const __gri
     for (int e = 0; e < 8; ++e) v[e] = __ldg(src + t + e * T);   // stage-0 positions t + e P/16 < N
 #pragma unroll
     for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);   // the expanded half, never loaded
+    if constexpr (FAC) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = cmul(v[e], __ldg(pre + t + e * T));
+    }
     const TwTable<P> twt{tw, t};
     fwd_from<P, R, PadLayout<P, R>, 0, 8, 0>(v, sm, r, t, twt);
     const float2* hh = h + item * h_item_stride + t;
@@ -68,7 +76,10 @@ k_line_conv(const float2* __restrict__ in, long long in_item_stride, const __gri
     // kept positions t + e T (e < 8): tile index (t + e T) R + r = e R T + threadIdx.x; the
     // exchange region is free after the trailing barrier of the last exchange
 #pragma unroll
-    for (int e = 0; e < 8; ++e) sm[e * NT + threadIdx.x] = cscale(v[e], scale);
+    for (int e = 0; e < 8; ++e) {
+        const float2 w = cscale(v[e], scale);
+        sm[e * NT + threadIdx.x] = FAC ? cmul(w, __ldg(post + t + e * T)) : w;
+    }
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -93,11 +104,12 @@ __host__ __device__ constexpr size_t line_p_smem_bytes() {
     return (line_smem_words<P, R>() + (size_t)R * line_stage_stride<P>()) * sizeof(float2) + sizeof(uint64_t);
 }
 
-template <int P, int R>
+template <int P, int R, bool FAC>
 __global__ void __launch_bounds__((R / 2) * (P / 16), (R / 2) * (P / 16) >= 512 ? 1 : 2)
 k_line_conv_p(const float2* __restrict__ in, long long in_item_stride, const __grid_constant__ CUtensorMap omap,
               const float2* __restrict__ h, long long h_item_stride, int conj, float scale,
-              const float4* __restrict__ tw, int groups_per_item, int total_groups, int* status) {
+              const float4* __restrict__ tw, int groups_per_item, int total_groups, int* status,
+              const float2* __restrict__ pre, const float2* __restrict__ post) {
     pdl_wait();
     constexpr int T = P / 16, N = P / 2, SST = line_stage_stride<P>();
     constexpr int BOX = N < kTmaBoxCols ? N : kTmaBoxCols;
@@ -130,6 +142,14 @@ k_line_conv_p(const float2* __restrict__ in, long long in_item_stride, const __g
         }
 #pragma unroll
         for (int e = 8; e < 16; ++e) { a[e] = make_float2(0.f, 0.f); b[e] = make_float2(0.f, 0.f); }
+        if constexpr (FAC) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float2 f = __ldg(pre + t + e * T);
+                a[e] = cmul(a[e], f);
+                b[e] = cmul(b[e], f);
+            }
+        }
         fence_proxy_async_smem();   // these reads of the staging buffer precede the next bulk copy into it
         if (__syncthreads_or(!ok)) break;                                // a copy did not land
         if (threadIdx.x == 0 && g + (int)gridDim.x < total_groups) issue(g + gridDim.x);
@@ -155,7 +175,12 @@ k_line_conv_p(const float2* __restrict__ in, long long in_item_stride, const __g
         // kept positions t + e T (e < 8) of lines c0, c0 + 1: tile words (t + e T) R + c0, + 1
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const float2 x = cscale(a[e], scale), y = cscale(b[e], scale);
+            float2 x = cscale(a[e], scale), y = cscale(b[e], scale);
+            if constexpr (FAC) {
+                const float2 q = __ldg(post + t + e * T);
+                x = cmul(x, q);
+                y = cmul(y, q);
+            }
             *reinterpret_cast<float4*>(sm + (t + e * T) * R + c0) = make_float4(x.x, x.y, y.x, y.y);
         }
         fence_proxy_async_smem();
@@ -170,10 +195,11 @@ k_line_conv_p(const float2* __restrict__ in, long long in_item_stride, const __g
     if (threadIdx.x == 0) tma_store_wait_read();
 }
 
-template <int P>
+template <int P, bool FAC>
 static cudaError_t line_conv_impl(const float2* in, long long in_item_stride, const CUtensorMap* omap, int lines,
                                   int items, const float2* h, long long h_item_stride, int conj, float scale,
-                                  const float4* tw, int* status, cudaStream_t st) {
+                                  const float4* tw, int* status, const float2* pre, const float2* post,
+                                  cudaStream_t st) {
     constexpr int R = line_rows<P>();
     constexpr int T = P / 16;
     if (lines % R || items < 1 || items > 65535) return cudaErrorInvalidValue;
@@ -181,19 +207,19 @@ static cudaError_t line_conv_impl(const float2* in, long long in_item_stride, co
     if (P >= 512 && aligned && status) {
         const size_t smem = line_p_smem_bytes<P, R>();
         int resident = 0;
-        cudaError_t e = kernel_setup<k_line_conv_p<P, R>>(smem, (R / 2) * T, &resident);
+        cudaError_t e = kernel_setup<k_line_conv_p<P, R, FAC>>(smem, (R / 2) * T, &resident);
         if (e != cudaSuccess) return e;
         const int groups = (lines / R) * items;
         const int grid = std::min(groups, resident);
         if (grid > 0)
-            return pdl_launch(k_line_conv_p<P, R>, dim3(grid), dim3((R / 2) * T), smem, st, in, in_item_stride, *omap,
-                              h, h_item_stride, conj, scale, tw, lines / R, groups, status);
+            return pdl_launch(k_line_conv_p<P, R, FAC>, dim3(grid), dim3((R / 2) * T), smem, st, in, in_item_stride,
+                              *omap, h, h_item_stride, conj, scale, tw, lines / R, groups, status, pre, post);
     }
     const size_t smem = line_smem_words<P, R>() * sizeof(float2);
-    cudaError_t e = kernel_setup<k_line_conv<P, R>>(smem, R * T, nullptr);
+    cudaError_t e = kernel_setup<k_line_conv<P, R, FAC>>(smem, R * T, nullptr);
     if (e != cudaSuccess) return e;
-    return pdl_launch(k_line_conv<P, R>, dim3(lines / R, items), dim3(R * T), smem, st, in, in_item_stride, *omap, h,
-                      h_item_stride, conj, scale, tw);
+    return pdl_launch(k_line_conv<P, R, FAC>, dim3(lines / R, items), dim3(R * T), smem, st, in, in_item_stride,
+                      *omap, h, h_item_stride, conj, scale, tw, pre, post);
 }
 
 int line_block_rows(int p) {
@@ -207,9 +233,11 @@ int line_block_rows(int p) {
 
 cudaError_t launch_line_conv(int p, const float2* in, long long in_item_stride, const CUtensorMap* omap, int lines,
                              int items, const float2* h, long long h_item_stride, int conj, float scale,
-                             const float4* tw, int* status, cudaStream_t st) {
+                             const float4* tw, int* status, const float2* pre, const float2* post, cudaStream_t st) {
+    if (!pre != !post) return cudaErrorInvalidValue;
     switch (p) {
-#define CASE(P) case P: return line_conv_impl<P>(in, in_item_stride, omap, lines, items, h, h_item_stride, conj, scale, tw, status, st);
+#define CASE(P) case P: return pre ? line_conv_impl<P, true>(in, in_item_stride, omap, lines, items, h, h_item_stride, conj, scale, tw, status, pre, post, st) \
+                               : line_conv_impl<P, false>(in, in_item_stride, omap, lines, items, h, h_item_stride, conj, scale, tw, status, nullptr, nullptr, st);
         CASE(32) CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024) CASE(2048) CASE(4096) CASE(8192)
 #undef CASE
         default: return cudaErrorInvalidValue;

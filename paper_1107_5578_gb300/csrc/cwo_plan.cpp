@@ -269,7 +269,7 @@ cwo_status ensure_scratch(cwo_plan* p, int items) {
     if (st != CWO_OK) return st;
     if ((e = cwo::make_intermediate_map(&p->wmap_f, p->scratch, p->ny, p->px, items, cwo::row_block_rows(p->px, false))) ||
         (e = cwo::make_intermediate_map(&p->wmap_i, p->scratch, p->ny, p->px, items, cwo::row_block_rows(p->px, true))) ||
-        (p->type == CWO_FRESNEL_CONV &&
+        ((p->type == CWO_FRESNEL_CONV || p->type == CWO_SHIFTED_FRESNEL) &&
          (e = cwo::make_intermediate_map(&p->wmap_s, p->scratch, p->ny, p->nx, items, cwo::line_block_rows(p->px)))))
         return cuda_fail(e, "tensor map of the intermediate");
     p->scap = items;
@@ -528,19 +528,27 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     float2* fout = (float2*)out;
     cudaError_t e;
     const float scale = (float)(1.0 / ((double)p->px * (double)p->py));
-    if (p->type == CWO_FRESNEL_CONV && !stack && ep.mode == cwo::EPI_NONE && (uintptr_t)out % 16 == 0) {
+    const bool separable = p->type == CWO_FRESNEL_CONV || p->type == CWO_SHIFTED_FRESNEL;
+    if (separable && !stack && epi.mode == cwo::EPI_NONE && (uintptr_t)out % 16 == 0) {
         // separable form: a padded line convolution along x into the column-major Nx x Ny
-        // intermediate, then one along y into the output (cwo_lines.cu)
+        // intermediate, then one along y into the output (cwo_lines.cu); the shifted form
+        // multiplies each pass's input by the source factor and its output by the destination
+        // factor of its axis
+        const bool sf = p->type == CWO_SHIFTED_FRESNEL;
+        const float2* prex = sf ? pre.fx : nullptr;
+        const float2* prey = sf ? pre.fy : nullptr;
+        const float2* postx = sf ? ep.qx : nullptr;
+        const float2* posty = sf ? ep.qy : nullptr;
         CUtensorMap omap;
         if ((e = cwo::make_intermediate_map(&omap, out, p->nx, p->ny, batch, cwo::line_block_rows(p->py))))
             return cuda_fail(e, "tensor map of the output");
         const long long istr = in_stride ? in_stride : field;
         if ((e = mark(0)) ||
             (e = cwo::launch_line_conv(p->px, fin, istr, &p->wmap_s, p->ny, batch, hp.hx, hp.x_item_stride, hp.conj,
-                                       (float)(1.0 / p->px), p->tw_x, p->status, s)) ||
+                                       (float)(1.0 / p->px), p->tw_x, p->status, prex, postx, s)) ||
             (e = mark(1)) ||
             (e = cwo::launch_line_conv(p->py, p->scratch, field, &omap, p->nx, batch, hp.hy, hp.y_item_stride, hp.conj,
-                                       (float)(1.0 / p->py), p->tw_y, p->status, s)) ||
+                                       (float)(1.0 / p->py), p->tw_y, p->status, prey, posty, s)) ||
             (e = mark(2)) || (e = mark(3)))
             return cuda_fail(e, "separable Fresnel launch");
         return CWO_OK;
@@ -959,7 +967,7 @@ cwo_status cwo_gs_run(cwo_plan* plan, const float* amplitude, void* field_c64, f
 
 int cwo_launches_per_call(const cwo_plan* plan) {
     if (!plan) return 0;
-    return plan->type == CWO_FRESNEL_FOURIER || plan->type == CWO_FRESNEL_CONV ? 2 : 3;
+    return plan->type == CWO_FRESNEL_FOURIER || plan->type == CWO_FRESNEL_CONV || plan->type == CWO_SHIFTED_FRESNEL ? 2 : 3;
 }
 
 cwo_status cwo_plan_check(cwo_plan* plan) {

@@ -79,3 +79,24 @@ def test_shifted_fresnel_literal_scale_and_rejections(cwo):
     assert e.value.status == cwo.ERR_UNSUPPORTED
     with pytest.raises(cwo.CwoError):
         cwo.Plan(64, 64, 8e-6, 8e-6, 532e-9, 0.05, shifted_fresnel=cwo.ShiftedFresnel(0.0, 5e-6, 0, 0, 0, 0))
+
+
+@pytest.mark.parametrize("case", CASES[1:])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_shifted_fresnel_two_passes_equal_three(cwo, case, adjoint):
+    # the plan runs two separable line passes (source and destination factors fused per axis);
+    # an output off a 16-byte boundary takes the three-pass method: the two agree
+    import torch
+    nx, ny, dx0, dy0, lam, z, prm = case
+    plan = cwo.Plan(nx, ny, dx0, dy0, lam, z, shifted_fresnel=cwo.ShiftedFresnel(*prm))
+    assert plan.launches_per_call == 2
+    x = torch.from_numpy(synth.random_field(nx, seed=74, ny=ny).astype(np.complex64)).cuda()
+    run = plan.adjoint if adjoint else plan.propagate
+    a = run(x).cpu().numpy().astype(np.complex128)
+    buf = torch.empty(nx * ny + 1, dtype=torch.complex64, device="cuda")
+    out = buf[1:].view(ny, nx)
+    run(x, out=out)
+    b = out.cpu().numpy().astype(np.complex128)
+    plan.check()
+    plan.close()
+    assert _rel(a, b) <= 1e-5
