@@ -46,8 +46,9 @@ cwo_status cwo_debug_asm_axis(int p, double pitch, double lambda, double z, int 
 cwo_status cwo_debug_asm_h(int px, int py, double dx, double dy, double lambda, double z, int* mode_out,
                            float* out_ri);
 
-/* Host emulation of the three CUDA passes for one [ny][nx] complex64 field (same butterflies,
- * stage positions, tables and transfer-function code, executed serially on the CPU).  type is
+/* Host emulation of the CUDA passes for one [ny][nx] complex64 field (same butterflies, stage
+ * positions, tables and transfer-function code, executed serially on the CPU): the three passes
+ * of the angular spectrum method, the two separable line passes of the Fresnel form.  type is
  * CWO_ANGULAR or CWO_FRESNEL_CONV, flags 0 or CWO_FLAG_LITERAL_SCALE, adjoint 0/1.  in_ri and
  * out_ri: 2 nx ny floats each, caller-owned host memory.  Slow; meant for small fields. */
 cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, double lambda, double z,

@@ -6,6 +6,7 @@
 // machine without a GPU.  It is slow and only meant for small fields.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -135,8 +136,27 @@ extern "C" cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, do
     const double sy = lambda * lambda / ((double)py * dy * (double)py * dy);
     const float2* in = (const float2*)in_ri;
     float2* out = (float2*)out_ri;
-    std::vector<float2> W((size_t)ny * px);
     LineFn fx = pick_fwd(px), ix = pick_inv(px), fy = pick_fwd(py), iy = pick_inv(py);
+    if (fresnel) {
+        // the two separable line passes (cwo_lines.cu): rows with Hx into a column-major Nx x Ny
+        // intermediate, then its columns with Hy into the output; each scaled by 1/P of its axis
+        std::vector<float2> M((size_t)nx * ny), line((size_t)std::max(px, py)), half((size_t)std::max(nx, ny));
+        const float scx = (float)(1.0 / px), scy = (float)(1.0 / py);
+        for (int y = 0; y < ny; ++y) {
+            fx(in + (size_t)y * nx, 1, line.data(), 1, twx.data());
+            for (int i = 0; i < px; ++i) line[i] = adjoint ? cmulc(line[i], hx[i]) : cmul(line[i], hx[i]);
+            ix(line.data(), 1, half.data(), 1, twx.data());
+            for (int x = 0; x < nx; ++x) M[(size_t)x * ny + y] = cscale(half[x], scx);
+        }
+        for (int x = 0; x < nx; ++x) {
+            fy(M.data() + (size_t)x * ny, 1, line.data(), 1, twy.data());
+            for (int i = 0; i < py; ++i) line[i] = adjoint ? cmulc(line[i], hy[i]) : cmul(line[i], hy[i]);
+            iy(line.data(), 1, half.data(), 1, twy.data());
+            for (int y = 0; y < ny; ++y) out[(size_t)y * nx + x] = cscale(half[y], scy);
+        }
+        return CWO_OK;
+    }
+    std::vector<float2> W((size_t)ny * px);
     for (int y = 0; y < ny; ++y) fx(in + (size_t)y * nx, 1, W.data() + (size_t)y * px, 1, twx.data());
     std::vector<float2> col(py);
     for (int c = 0; c < px; ++c) {

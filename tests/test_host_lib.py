@@ -158,6 +158,7 @@ def test_asm_axis_phase_reduction_is_exact(lib, p, pitch, lam, z):
 @pytest.mark.parametrize("nx,ny,kind,z,pitch", [
     (16, 16, 0, 0.05, 10e-6), (32, 16, 0, 1e-3, 1e-6), (16, 64, 1, 0.02, 10e-6),
     (64, 64, 1, 0.08, 8e-6), (64, 32, 0, 20e-6, 0.4e-6), (128, 128, 0, -0.1, 10e-6),
+    (128, 32, 1, -0.3, 6e-6), (256, 16, 1, 0.01, 4e-6),
 ])
 @pytest.mark.parametrize("adjoint", [0, 1])
 def test_host_emulation_of_the_kernels_matches_the_oracle(lib, nx, ny, kind, z, pitch, adjoint):
