@@ -261,7 +261,8 @@ cwo_status cwo_gs_run(cwo_plan* plan, const float* amplitude, void* field_c64, f
 /* Number of kernel launches one call of cwo_propagate_batch makes for this plan (for launch
  * accounting in benchmarks): 3 for the angular spectrum types, 2 for the Fresnel Fourier form and
  * for the Fresnel convolution and shifted Fresnel types, whose separable line passes take 2 (3
- * for a shared-source z-stack, an output epilogue, or an output not on a 16-byte boundary). */
+ * for an output epilogue, an output or a stack source not on a 16-byte boundary, a shifted
+ * Fresnel z-stack, or a z-stack of padded rows longer than 4096). */
 int cwo_launches_per_call(const cwo_plan* plan);
 
 /* Synchronise the device and report whether any earlier call on this plan had a bounded wait

@@ -111,6 +111,13 @@ cudaError_t launch_build_hcache(float2* out, int npairs, int py, const HParams& 
 // transposed through omap (dims: lines, P/2 positions, items; boxes of line_block_rows(P) lines).
 // pre and post: both or neither.
 int line_block_rows(int p);
+// first pass of a shared-source z-stack: `lines` source lines (one item) transformed once and
+// stored per plane j (item j of omap) after the multiply by h + j * h_item_stride; 512 <= p <= 4096
+// and a 16-byte aligned source
+bool line_stack_supported(int p);
+cudaError_t launch_line_stack(int p, const float2* in, const CUtensorMap* omap, int lines, int planes, const float2* h,
+                              long long h_item_stride, int conj, float scale, const float4* tw, int* status,
+                              cudaStream_t st);
 cudaError_t launch_line_conv(int p, const float2* in, long long in_item_stride, const CUtensorMap* omap, int lines,
                              int items, const float2* h, long long h_item_stride, int conj, float scale,
                              const float4* tw, int* status, const float2* pre, const float2* post, cudaStream_t st);

@@ -195,6 +195,106 @@ k_line_conv_p(const float2* __restrict__ in, long long in_item_stride, const __g
     if (threadIdx.x == 0) tma_store_wait_read();
 }
 
+// Shared-source z-stack, first pass: each source line is transformed once and its spectrum kept in
+// registers; for every plane j it is multiplied by that plane's axis table, transformed back and
+// stored into plane j's intermediate (item j of omap).  The second pass is k_line_conv_p over the
+// planes.  One line per thread (spectrum and working copy: 32 values), R lines per group as in
+// line_rows, persistent with staged bulk loads as k_line_conv_p.
+template <int P, int R>
+__global__ void __launch_bounds__(R * (P / 16), 1)
+k_line_stack_p(const float2* __restrict__ in, const __grid_constant__ CUtensorMap omap, const float2* __restrict__ h,
+               long long h_item_stride, int planes, int conj, float scale, const float4* __restrict__ tw,
+               int groups, int* status) {
+    pdl_wait();
+    constexpr int T = P / 16, N = P / 2, NT = R * T, SST = line_stage_stride<P>();
+    constexpr int BOX = N < kTmaBoxCols ? N : kTmaBoxCols;
+    using Lay = PadLayout<P, R>;
+    extern __shared__ __align__(1024) float2 sm[];
+    float2* stage = sm + line_smem_words<P, R>();
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(stage + R * SST);
+    const int r = threadIdx.x % R, t = threadIdx.x / R;
+    auto issue = [&](int g) {   // thread 0: the R source lines of group g into the staging buffer
+        const float2* src = in + (long long)g * R * N;
+        mbar_arrive_expect_tx(mbar, (unsigned)(R * N * sizeof(float2)));
+#pragma unroll 1
+        for (int rr = 0; rr < R; ++rr) bulk_load(stage + rr * SST, src + rr * N, (unsigned)(N * sizeof(float2)), mbar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        if ((int)blockIdx.x < groups) issue(blockIdx.x);
+    }
+    __syncthreads();
+    const TwTable<P> twt{tw, t};
+    unsigned parity = 0;
+#pragma unroll 1
+    for (int g = blockIdx.x; g < groups; g += gridDim.x, parity ^= 1u) {
+        const bool ok = mbar_wait_bounded(mbar, parity, status);
+        float2 spec[16];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) spec[e] = stage[r * SST + t + e * T];   // stage-0 positions t + e P/16
+#pragma unroll
+        for (int e = 8; e < 16; ++e) spec[e] = make_float2(0.f, 0.f);
+        fence_proxy_async_smem();   // these reads of the staging buffer precede the next bulk copy into it
+        if (__syncthreads_or(!ok)) break;                                // a copy did not land
+        if (threadIdx.x == 0 && g + (int)gridDim.x < groups) issue(g + gridDim.x);
+        stage_butterflies<P, 0, false, 8>(spec);
+        if constexpr (Geo<P>::NST > 1) twt.template apply<0, false>(spec);
+        if (threadIdx.x == 0) tma_store_wait_read();                      // previous tile read out
+        __syncthreads();
+        if constexpr (Geo<P>::NST > 1) {
+            exchange<P, R, Lay, 0, 1, 0, 0>(sm, r, t, spec);
+            fwd_from<P, R, Lay, 1, 8, 0>(spec, sm, r, t, twt);
+        }
+#pragma unroll 1
+        for (int j = 0; j < planes; ++j) {
+            float2 v[16];
+            const float2* hh = h + j * h_item_stride + t;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float2 w = __ldg(hh + e * T);
+                v[e] = conj ? cmulc(spec[e], w) : cmul(spec[e], w);
+            }
+            if (j > 0) {   // the previous plane's tile (which aliases the exchange region) read out
+                if (threadIdx.x == 0) tma_store_wait_read();
+                __syncthreads();
+            }
+            inv_from<P, R, Lay, Geo<P>::NST - 1, 0, 0>(v, sm, r, t, twt);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) sm[e * NT + threadIdx.x] = cscale(v[e], scale);
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+#pragma unroll 1
+                for (int bx = 0; bx < N / BOX; ++bx) tma_store_3d(&omap, sm + bx * BOX * R, g * R, bx * BOX, j);
+                tma_store_commit();
+            }
+        }
+    }
+    if (threadIdx.x == 0) tma_store_wait_read();
+}
+
+template <int P>
+static cudaError_t line_stack_impl(const float2* in, const CUtensorMap* omap, int lines, int planes, const float2* h,
+                                   long long h_item_stride, int conj, float scale, const float4* tw, int* status,
+                                   cudaStream_t st) {
+    constexpr int R = line_rows<P>();
+    constexpr int T = P / 16;
+    if constexpr (P < 512 || P > 4096) {
+        return cudaErrorNotSupported;
+    } else {
+        if (lines % R || planes < 1 || !status || (uintptr_t)in % 16) return cudaErrorInvalidValue;
+        const size_t smem = line_p_smem_bytes<P, R>();
+        int resident = 0;
+        cudaError_t e = kernel_setup<k_line_stack_p<P, R>>(smem, R * T, &resident);
+        if (e != cudaSuccess) return e;
+        const int groups = lines / R;
+        const int grid = std::min(groups, resident);
+        if (grid < 1) return cudaErrorInvalidConfiguration;
+        return pdl_launch(k_line_stack_p<P, R>, dim3(grid), dim3(R * T), smem, st, in, *omap, h, h_item_stride, planes,
+                          conj, scale, tw, groups, status);
+    }
+}
+
 template <int P, bool FAC>
 static cudaError_t line_conv_impl(const float2* in, long long in_item_stride, const CUtensorMap* omap, int lines,
                                   int items, const float2* h, long long h_item_stride, int conj, float scale,
@@ -228,6 +328,19 @@ int line_block_rows(int p) {
         CASE(32) CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024) CASE(2048) CASE(4096) CASE(8192)
 #undef CASE
         default: return 0;
+    }
+}
+
+bool line_stack_supported(int p) { return p >= 512 && p <= 4096; }
+
+cudaError_t launch_line_stack(int p, const float2* in, const CUtensorMap* omap, int lines, int planes, const float2* h,
+                              long long h_item_stride, int conj, float scale, const float4* tw, int* status,
+                              cudaStream_t st) {
+    switch (p) {
+#define CASE(P) case P: return line_stack_impl<P>(in, omap, lines, planes, h, h_item_stride, conj, scale, tw, status, st);
+        CASE(32) CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024) CASE(2048) CASE(4096) CASE(8192)
+#undef CASE
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -528,6 +528,23 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
     float2* fout = (float2*)out;
     cudaError_t e;
     const float scale = (float)(1.0 / ((double)p->px * (double)p->py));
+    if (p->type == CWO_FRESNEL_CONV && stack && epi.mode == cwo::EPI_NONE && (uintptr_t)out % 16 == 0 &&
+        (uintptr_t)in % 16 == 0 && cwo::line_stack_supported(p->px)) {
+        // shared-source stack in the separable form: every source row transformed once and
+        // convolved per plane into that plane's intermediate, then every plane's columns
+        CUtensorMap omap;
+        if ((e = cwo::make_intermediate_map(&omap, out, p->nx, p->ny, batch, cwo::line_block_rows(p->py))))
+            return cuda_fail(e, "tensor map of the output");
+        if ((e = mark(0)) ||
+            (e = cwo::launch_line_stack(p->px, fin, &p->wmap_s, p->ny, batch, hp.hx, hp.x_item_stride, hp.conj,
+                                        (float)(1.0 / p->px), p->tw_x, p->status, s)) ||
+            (e = mark(1)) ||
+            (e = cwo::launch_line_conv(p->py, p->scratch, field, &omap, p->nx, batch, hp.hy, hp.y_item_stride, hp.conj,
+                                       (float)(1.0 / p->py), p->tw_y, p->status, nullptr, nullptr, s)) ||
+            (e = mark(2)) || (e = mark(3)))
+            return cuda_fail(e, "separable Fresnel stack launch");
+        return CWO_OK;
+    }
     const bool separable = p->type == CWO_FRESNEL_CONV || p->type == CWO_SHIFTED_FRESNEL;
     if (separable && !stack && epi.mode == cwo::EPI_NONE && (uintptr_t)out % 16 == 0) {
         // separable form: a padded line convolution along x into the column-major Nx x Ny
