@@ -24,7 +24,9 @@
  *   - evanescent bins of H_A (negative radicand) are set to 0
  *   - the Fresnel transfer function is the DFT of h_F sampled on the padded grid (index i maps
  *     to displacement i for i < P/2, i - P otherwise); h_F is separable, so it is formed as the
- *     outer product of two 1-D DFTs computed once per plan in double precision
+ *     outer product of two 1-D DFTs computed once per plan in double precision, and the 2-D
+ *     padded convolution is computed as a padded 1-D convolution of every row followed by one of
+ *     every column (the same linear convolution, up to rounding)
  *   - C includes the area element dx*dy of the discretised integral (CWO_FLAG_LITERAL_SCALE
  *     drops it, which is the paper's printed coefficient)
  *   - defaults (Section "CWO class", paragraph after Eq. norm): wavelength 633 nm, pitch 10 um;
