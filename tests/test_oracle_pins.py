@@ -77,6 +77,28 @@ def test_fresnel_fft_equals_direct_sum(nx, ny, flags):
     assert rel(a, b) < 1e-12
 
 
+@pytest.mark.parametrize("nx,ny,z", [(64, 128, 0.02), (128, 32, -0.05)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_fresnel_is_a_row_then_column_convolution(nx, ny, z, adjoint):
+    # the discretised Fresnel integral (Eq. fre_conv) with its separable chirp is
+    # u2 = C * Hy @ u1 @ Hx^T, Hx[m2, m1] = exp(i pi ((m2 - m1) dx)^2 / (lambda z)): one linear
+    # convolution along every row, then one along every column; the padded 2-D FFT method
+    # computes exactly that (adjoint: conj(C) with the conjugate, symmetric chirp matrices)
+    dx, dy = PITCH, 0.8 * PITCH
+    u = synth.random_field(nx, seed=12, ny=ny)
+    mx = np.arange(nx)
+    my = np.arange(ny)
+    hx = np.exp(1j * np.pi * ((mx[:, None] - mx[None, :]) * dx) ** 2 / (LAM * z))
+    hy = np.exp(1j * np.pi * ((my[:, None] - my[None, :]) * dy) ** 2 / (LAM * z))
+    c = dx * dy * np.exp(2j * np.pi * z / LAM) / (1j * LAM * z)
+    if adjoint:
+        want = np.conj(c) * np.conj(hy) @ u @ np.conj(hx).T
+    else:
+        want = c * hy @ u @ hx.T
+    got = oracle.propagate(u, dx, dy, LAM, z, kind=oracle.FRESNEL_CONV, flags=oracle.ADJOINT if adjoint else 0)
+    assert rel(got, want) < 1e-10
+
+
 @pytest.mark.parametrize("nx,ny,dx,dy,z", [
     (8, 8, 1e-6, 1e-6, 1e-4),        # several cycles of phase across the band
     (16, 8, 1e-6, 2e-6, 3e-4),
