@@ -46,6 +46,14 @@ cwo_status cwo_debug_asm_axis(int p, double pitch, double lambda, double z, int 
 cwo_status cwo_debug_asm_h(int px, int py, double dx, double dy, double lambda, double z, int* mode_out,
                            float* out_ri);
 
+/* Host emulation of the shifted Fresnel plan of cwo_plan_create_shifted_fresnel (flags 0) for one
+ * [ny][nx] complex64 field: the same tables and the two separable line passes with the source
+ * and destination factors of each axis (adjoint 0/1).  in_ri, out_ri: 2 nx ny floats each,
+ * caller-owned host memory.  Slow; meant for small fields. */
+cwo_status cwo_debug_emulate_shifted_fresnel(int nx, int ny, double dx0, double dy0, double lambda, double z,
+                                             const cwo_shifted_fresnel* params, int adjoint, const float* in_ri,
+                                             float* out_ri);
+
 /* Host emulation of the CUDA passes for one [ny][nx] complex64 field (same butterflies, stage
  * positions, tables and transfer-function code, executed serially on the CPU): the three passes
  * of the angular spectrum method, the two separable line passes of the Fresnel form.  type is

@@ -179,6 +179,48 @@ extern "C" cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, do
     return CWO_OK;
 }
 
+extern "C" cwo_status cwo_debug_emulate_shifted_fresnel(int nx, int ny, double dx0, double dy0, double lambda,
+                                                        double z, const cwo_shifted_fresnel* prm, int adjoint,
+                                                        const float* in_ri, float* out_ri) {
+    using namespace cwo;
+    using namespace cwo::host;
+    if (!prm || !in_ri || !out_ri || nx < 16 || ny < 16 || nx > 4096 || ny > 4096 || (nx & (nx - 1)) ||
+        (ny & (ny - 1)) || !(dx0 > 0) || !(dy0 > 0) || !(prm->dx1 > 0) || !(prm->dy1 > 0) || !(lambda > 0) ||
+        !std::isfinite(z) || z == 0.0)
+        return CWO_ERR_INVALID_ARG;
+    const int px = 2 * nx, py = 2 * ny;
+    const std::vector<float4> twx = twiddle_table(AxisGeo(px)), twy = twiddle_table(AxisGeo(py));
+    std::vector<float2> fx(nx), fy(ny), qx(nx), qy(ny), hx(px), hy(py);
+    const double cph = 6.283185307179586476925286766559 * frac01(z / lambda);
+    const cd C = cd(std::cos(cph), std::sin(cph)) / cd(0.0, lambda * z) * (dx0 * dy0);
+    shifted_fresnel_axis(nx, dx0, prm->dx1, prm->ox0, prm->ox1, lambda, z, C, fx.data(), qx.data(), hx.data());
+    shifted_fresnel_axis(ny, dy0, prm->dy1, prm->oy0, prm->oy1, lambda, z, cd(1.0, 0.0), fy.data(), qy.data(), hy.data());
+    auto conj = [](float2 a) { return make_float2(a.x, -a.y); };
+    // the two separable line passes of cwo_lines.cu with the factors of their axis:
+    // forward pre = f, post = q; adjoint pre = conj(q), post = conj(f), conj(h)
+    const float2* in = (const float2*)in_ri;
+    float2* out = (float2*)out_ri;
+    LineFn fwx = pick_fwd(px), ivx = pick_inv(px), fwy = pick_fwd(py), ivy = pick_inv(py);
+    std::vector<float2> M((size_t)nx * ny), src((size_t)std::max(nx, ny)), line((size_t)std::max(px, py)),
+        half((size_t)std::max(nx, ny));
+    const float scx = (float)(1.0 / px), scy = (float)(1.0 / py);
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) src[x] = cmul(in[(size_t)y * nx + x], adjoint ? conj(qx[x]) : fx[x]);
+        fwx(src.data(), 1, line.data(), 1, twx.data());
+        for (int i = 0; i < px; ++i) line[i] = adjoint ? cmulc(line[i], hx[i]) : cmul(line[i], hx[i]);
+        ivx(line.data(), 1, half.data(), 1, twx.data());
+        for (int x = 0; x < nx; ++x) M[(size_t)x * ny + y] = cmul(cscale(half[x], scx), adjoint ? conj(fx[x]) : qx[x]);
+    }
+    for (int x = 0; x < nx; ++x) {
+        for (int y = 0; y < ny; ++y) src[y] = cmul(M[(size_t)x * ny + y], adjoint ? conj(qy[y]) : fy[y]);
+        fwy(src.data(), 1, line.data(), 1, twy.data());
+        for (int i = 0; i < py; ++i) line[i] = adjoint ? cmulc(line[i], hy[i]) : cmul(line[i], hy[i]);
+        ivy(line.data(), 1, half.data(), 1, twy.data());
+        for (int y = 0; y < ny; ++y) out[(size_t)y * nx + x] = cmul(cscale(half[y], scy), adjoint ? conj(fy[y]) : qy[y]);
+    }
+    return CWO_OK;
+}
+
 extern "C" cwo_status cwo_debug_asm_h(int px, int py, double dx, double dy, double lambda, double z, int* mode_out,
                                       float* out_ri) {
     using namespace cwo;

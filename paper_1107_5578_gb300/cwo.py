@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
                 "cwo_debug_emulate": ([i, i, d, d, d, d, i, u, i, vp, vp], i),
                 "cwo_debug_line_fft": ([i, i, vp, vp], i),
                 "cwo_debug_asm_h": ([i, i, d, d, d, d, ctypes.POINTER(ctypes.c_int), vp], i),
+                "cwo_debug_emulate_shifted_fresnel": ([i, i, d, d, d, d, ctypes.POINTER(ShiftedFresnel), i, vp, vp], i),
                 "cwo_debug_bounded_wait": ([u, i, ctypes.POINTER(ctypes.c_int)], i),
             }
             for name, (args, res) in sig.items():
@@ -383,6 +384,19 @@ def asm_h(px, py, dx, dy, wavelength, z):
     check(lib().cwo_debug_asm_h(px, py, dx, dy, wavelength, z, ctypes.byref(mode), out.ctypes.data),
           "cwo_debug_asm_h")
     return mode.value, out
+
+
+def emulate_shifted_fresnel(u, dx0, dy0, wavelength, z, params, adjoint=False):
+    """Host emulation of a shifted Fresnel plan's kernels (test support): numpy complex64
+    [ny][nx] -> same."""
+    import numpy as np
+    a = np.ascontiguousarray(u, dtype=np.complex64)
+    ny, nx = a.shape
+    out = np.empty_like(a)
+    check(lib().cwo_debug_emulate_shifted_fresnel(nx, ny, dx0, dy0, wavelength, z, ctypes.byref(params),
+                                                  int(adjoint), a.ctypes.data, out.ctypes.data),
+          "cwo_debug_emulate_shifted_fresnel")
+    return out
 
 
 def line_fft(x, inverse=False):
