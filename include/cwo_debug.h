@@ -46,6 +46,13 @@ cwo_status cwo_debug_asm_axis(int p, double pitch, double lambda, double z, int 
 cwo_status cwo_debug_asm_h(int px, int py, double dx, double dy, double lambda, double z, int* mode_out,
                            float* out_ri);
 
+/* Host emulation of the shifted angular-spectrum plan of cwo_plan_create_shifted (flags 0) for
+ * one [ny][nx] complex64 field: the same shifted, windowed per-axis tables and the three passes
+ * (adjoint 0/1).  CWO_ERR_UNSUPPORTED where the plan would evaluate its phase per element in
+ * FP64.  in_ri, out_ri: 2 nx ny floats each, caller-owned host memory.  Slow. */
+cwo_status cwo_debug_emulate_shifted(int nx, int ny, double dx, double dy, double lambda, double z,
+                                     const cwo_shift* shift, int adjoint, const float* in_ri, float* out_ri);
+
 /* Host emulation of the shifted Fresnel plan of cwo_plan_create_shifted_fresnel (flags 0) for one
  * [ny][nx] complex64 field: the same tables and the two separable line passes with the source
  * and destination factors of each axis (adjoint 0/1).  in_ri, out_ri: 2 nx ny floats each,

@@ -179,6 +179,43 @@ extern "C" cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, do
     return CWO_OK;
 }
 
+extern "C" cwo_status cwo_debug_emulate_shifted(int nx, int ny, double dx, double dy, double lambda, double z,
+                                                const cwo_shift* sh, int adjoint, const float* in_ri, float* out_ri) {
+    using namespace cwo;
+    using namespace cwo::host;
+    if (!sh || !in_ri || !out_ri || nx < 16 || ny < 16 || nx > 4096 || ny > 4096 || (nx & (nx - 1)) ||
+        (ny & (ny - 1)) || !(dx > 0) || !(dy > 0) || !(lambda > 0) || !std::isfinite(z))
+        return CWO_ERR_INVALID_ARG;
+    const int px = 2 * nx, py = 2 * ny;
+    const int tmode = asm_tail_mode(px, py, dx, dy, lambda, z);
+    if (tmode == 2) return CWO_ERR_UNSUPPORTED;   // the per-element FP64 arm is not emulated here
+    const std::vector<float4> twx = twiddle_table(AxisGeo(px)), twy = twiddle_table(AxisGeo(py));
+    std::vector<float4> ax(px), ay(py);
+    asm_axis_table_shifted(AxisGeo(px), dx, lambda, z, true, sh->ox, sh->cx, sh->wx, ax.data());
+    asm_axis_table_shifted(AxisGeo(py), dy, lambda, z, false, sh->oy, sh->cy, sh->wy, ay.data());
+    const float K = (float)(z / lambda);
+    const float2* in = (const float2*)in_ri;
+    float2* out = (float2*)out_ri;
+    LineFn fx = pick_fwd(px), ix = pick_inv(px), fy = pick_fwd(py), iy = pick_inv(py);
+    // the three passes: rows, columns with H (shift and windows folded into the tables), rows back
+    std::vector<float2> W((size_t)ny * px), col(py), line(nx);
+    for (int y = 0; y < ny; ++y) fx(in + (size_t)y * nx, 1, W.data() + (size_t)y * px, 1, twx.data());
+    for (int c = 0; c < px; ++c) {
+        fy(W.data() + c, px, col.data(), 1, twy.data());
+        for (int i = 0; i < py; ++i) {
+            const float2 h = tmode == 0 ? asm_h_reduced<true>(ax[c], ay[i], K) : asm_h_reduced<false>(ax[c], ay[i], K);
+            col[i] = adjoint ? cmulc(col[i], h) : cmul(col[i], h);
+        }
+        iy(col.data(), 1, W.data() + c, px, twy.data());
+    }
+    const float scale = (float)(1.0 / ((double)px * (double)py));
+    for (int y = 0; y < ny; ++y) {
+        ix(W.data() + (size_t)y * px, 1, line.data(), 1, twx.data());
+        for (int x = 0; x < nx; ++x) out[(size_t)y * nx + x] = cscale(line[x], scale);
+    }
+    return CWO_OK;
+}
+
 extern "C" cwo_status cwo_debug_emulate_shifted_fresnel(int nx, int ny, double dx0, double dy0, double lambda,
                                                         double z, const cwo_shifted_fresnel* prm, int adjoint,
                                                         const float* in_ri, float* out_ri) {

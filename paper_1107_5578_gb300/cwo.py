@@ -110,6 +110,7 @@ def lib() -> ctypes.CDLL:
                 "cwo_debug_line_fft": ([i, i, vp, vp], i),
                 "cwo_debug_asm_h": ([i, i, d, d, d, d, ctypes.POINTER(ctypes.c_int), vp], i),
                 "cwo_debug_emulate_shifted_fresnel": ([i, i, d, d, d, d, ctypes.POINTER(ShiftedFresnel), i, vp, vp], i),
+                "cwo_debug_emulate_shifted": ([i, i, d, d, d, d, ctypes.POINTER(Shift), i, vp, vp], i),
                 "cwo_debug_bounded_wait": ([u, i, ctypes.POINTER(ctypes.c_int)], i),
             }
             for name, (args, res) in sig.items():
@@ -384,6 +385,18 @@ def asm_h(px, py, dx, dy, wavelength, z):
     check(lib().cwo_debug_asm_h(px, py, dx, dy, wavelength, z, ctypes.byref(mode), out.ctypes.data),
           "cwo_debug_asm_h")
     return mode.value, out
+
+
+def emulate_shifted(u, dx, dy, wavelength, z, shift, adjoint=False):
+    """Host emulation of a shifted angular-spectrum plan's kernels (test support): numpy
+    complex64 [ny][nx] -> same."""
+    import numpy as np
+    a = np.ascontiguousarray(u, dtype=np.complex64)
+    ny, nx = a.shape
+    out = np.empty_like(a)
+    check(lib().cwo_debug_emulate_shifted(nx, ny, dx, dy, wavelength, z, ctypes.byref(shift), int(adjoint),
+                                          a.ctypes.data, out.ctypes.data), "cwo_debug_emulate_shifted")
+    return out
 
 
 def emulate_shifted_fresnel(u, dx0, dy0, wavelength, z, params, adjoint=False):

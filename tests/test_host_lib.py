@@ -235,3 +235,19 @@ def test_host_emulation_of_shifted_fresnel_matches_the_oracle(lib, nx, ny, dx0, 
     lhs = np.vdot(v.astype(np.complex128), got.astype(np.complex128))
     rhs = np.vdot(ahv.astype(np.complex128), u.astype(np.complex128))
     assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(got) * np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("n,dx,lam,z,shift", [
+    (64, 8e-6, 532e-9, 0.01, (200e-6, -120e-6, 0.0, 0.0, 0.0, 0.0)),              # shift only
+    (64, 8e-6, 532e-9, 0.05, (0.0, 0.0, 5e3, 2e4, -3e3, 1.5e4)),                   # windows only
+    (128, 4e-6, 633e-9, -0.02, (-80e-6, 40e-6, 1e4, 6e4, 0.0, 4e4)),               # both, z < 0
+])
+@pytest.mark.parametrize("adjoint", [0, 1])
+def test_host_emulation_of_shifted_asm_matches_the_oracle(lib, n, dx, lam, z, shift, adjoint):
+    # the shifted plan's tables (shift phase folded into W, windows as a = 2) and its three
+    # passes, run on the host, against the oracle's shifted ASM
+    u = synth.random_field(n, seed=77, ny=n // 2).astype(np.complex64)
+    sh = cwo.Shift(*shift)
+    got = cwo.emulate_shifted(u, dx, dx, lam, z, sh, adjoint=bool(adjoint))
+    want = oracle.propagate_shifted(u, dx, dx, lam, z, *shift, flags=oracle.ADJOINT if adjoint else 0)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-5
