@@ -310,7 +310,7 @@ def fresnel_batch_measurement(x, y, steps, hbm_peak):
     launches = plan.launches_per_call
     plan.close()
     gbs = 32 * N * N * B / (ms / 1e3) / 1e9
-    return {"workload": "fresnel_conv_2048_pad4096_batch16", "value": round(B / (ms / 1e3), 2), "unit": UNIT,
+    return {"workload": f"fresnel_conv_2048_pad4096_batch{B}", "value": round(B / (ms / 1e3), 2), "unit": UNIT,
             "passes_ms": {"line_x": round(pp[0], 4), "line_y": round(pp[1], 4)},
             "hbm_gbs_algorithmic": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm_peak, 4),
             "bytes_per_prop": 32 * N * N, "launches_per_call": launches}
