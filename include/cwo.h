@@ -194,6 +194,10 @@ cwo_status cwo_propagate(cwo_plan* plan, const void* in_c64, void* out_c64, void
  *                    distances; the per-item tables are computed in FP64 on the host and uploaded
  *                    stream-ordered.
  * Grows the scratch (synchronising) if `batch` exceeds the reserved size.
+ * Any complex64-aligned (8-byte) buffers are accepted; fields whose rows start on 16-byte
+ * boundaries take the kernels that move them by bulk and TMA copies (the fastest paths), others
+ * take per-thread loads (and, for a Fresnel output, the three-pass method): same results up to
+ * rounding.
  */
 cwo_status cwo_propagate_batch(cwo_plan* plan, const void* in, long long in_batch_stride,
                                void* out, int batch, const double* z_or_null, void* cuda_stream);
