@@ -295,6 +295,11 @@ cwo_status cwo_plan_set_timing_events(cwo_plan* plan, void* const* events);
  * CWO_ANGULAR plan.
  *   limits   nx, ny powers of two in [16, 1024] (the fixed scratch is 1024 x 2048 complex64,
  *            16 MiB); larger fields return CWO_ERR_INVALID_ARG without launching anything
+ *   errors   CWO_ERR_INVALID_ARG, before anything is enqueued, when a field is not 8-byte aligned
+ *            device memory of the current device or its allocation ends before nx * ny complex64
+ *            values; CWO_ERR_CUDA when a launch fails.  A bounded wait of the row passes that
+ *            expires (an asynchronous copy that never lands) is not reported by this entry point:
+ *            the output is then incomplete.  Each call clears that record before its passes.
  *   set-up   the first call on a device, with that device current, resolves the arrays'
  *            device addresses (cudaGetSymbolAddress); make that first call before any stream
  *            capture

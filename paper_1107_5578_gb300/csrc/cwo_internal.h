@@ -67,6 +67,9 @@ struct HParams {
 // launchers (return cudaGetLastError() after the launch)
 // Record the message returned by cwo_last_error() on this thread.
 void set_last_error(const char* msg);
+// Check that [ptr, ptr + bytes) is 8-byte aligned device (or managed) memory of `device` inside
+// one allocation (cuMemGetAddressRange); returns a cwo_status and sets the error message.
+int check_device_buffer(const void* ptr, size_t bytes, int device, const char* name);
 
 // The intermediate is column-major: [items][Px][Ny] complex64 (see cwo_rows.cu).
 // The row passes reach the intermediate through rank-3 TMA tensor maps (Ny, Px, items) with

@@ -59,19 +59,6 @@ cwo_status fail(cwo_status st, const char* msg) {
     return st;
 }
 
-// the fields must be device memory of the current device (a host pointer would fault the GPU)
-cwo_status check_field(const void* p, int dev, const char* what) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(CWO_ERR_INVALID_ARG, what);
-    }
-    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return fail(CWO_ERR_INVALID_ARG, what);
-    if (at.type == cudaMemoryTypeDevice && at.device != dev) return fail(CWO_ERR_INVALID_ARG, what);
-    if ((uintptr_t)p % 8) return fail(CWO_ERR_INVALID_ARG, what);
-    return CWO_OK;
-}
-
 // host addresses of the arrays, resolved once per device with that device current
 std::mutex g_mu;
 bool g_have[64];
@@ -137,8 +124,9 @@ struct AxisParams {
 };
 
 __global__ void k_setup(AxisParams ax, AxisParams ay, double lambda, double z, float4* tw_x, float4* tw_y,
-                        float4* tax, float4* tay, int* kbx, int* kby, int2* pairs, float* kf) {
+                        float4* tax, float4* tay, int* kbx, int* kby, int2* pairs, float* kf, int* status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) status[0] = 0;   // the row passes' bounded waits set it; each call starts clear
     for (int a = 0; a < 2; ++a) {
         const AxisParams g = a == 0 ? ax : ay;
         if (i >= g.P) continue;
@@ -213,8 +201,12 @@ extern "C" cwo_status cwo_propagate_asm_noalloc(int nx, int ny, double dx, doubl
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(CWO_ERR_CUDA, cudaGetErrorString(e));
     cwo_status st;
-    if ((st = check_field(in_c64, dev, "input: not 8-byte aligned device memory of the current device")) ||
-        (st = check_field(out_c64, dev, "output: not 8-byte aligned device memory of the current device")))
+    // both fields must be device memory of the current device, 8-byte aligned and large enough for
+    // nx * ny complex64 values inside one allocation (a host pointer or a short buffer would make
+    // the passes read or write memory that is not theirs)
+    const size_t field_bytes = (size_t)nx * (size_t)ny * 8u;
+    if ((st = (cwo_status)cwo::check_device_buffer(in_c64, field_bytes, dev, "input")) ||
+        (st = (cwo_status)cwo::check_device_buffer(out_c64, field_bytes, dev, "output")))
         return st;
     Addrs a{};
     if ((e = resolve(dev, &a)) != cudaSuccess) return fail(CWO_ERR_CUDA, cudaGetErrorString(e));
@@ -222,7 +214,7 @@ extern "C" cwo_status cwo_propagate_asm_noalloc(int nx, int ny, double dx, doubl
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const unsigned nthreads = 256, nblocks = (unsigned)((std::max(px, py) + nthreads - 1) / nthreads);
     k_setup<<<nblocks, nthreads, 0, s>>>(AxisParams{px, dx, true}, AxisParams{py, dy, false}, lambda, z, a.tw_x, a.tw_y,
-                                         a.ax, a.ay, a.kb_x, a.kb_y, a.pairs, a.kf);
+                                         a.ax, a.ay, a.kb_x, a.kb_y, a.pairs, a.kf, a.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(CWO_ERR_CUDA, cudaGetErrorString(e));
     cwo::HParams hp{};
     hp.mode = asm_mode(px, py, dx, dy, lambda, z);

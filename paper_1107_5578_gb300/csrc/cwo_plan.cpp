@@ -121,6 +121,10 @@ size_t tables_bytes(int nx, int ny) {
 
 void cwo::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
+int cwo::check_device_buffer(const void* ptr, size_t bytes, int device, const char* name) {
+    return check_device_range(ptr, bytes, device, name);
+}
+
 // ------------------------------------------------------------------------------------------
 // plan
 // ------------------------------------------------------------------------------------------
