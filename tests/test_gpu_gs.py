@@ -72,6 +72,71 @@ def test_gs_run_against_oracle(mods, n, iters):
     assert np.linalg.norm(got_i - int_o) / np.linalg.norm(int_o) <= 1e-3
 
 
+@pytest.mark.parametrize("n,iters", [(128, 4), (512, 3)])
+def test_gs_each_iteration_against_oracle_step(mods, n, iters):
+    """Every GS iterate of the device loop checked against one oracle step taken from it
+    (Section "GS algorithm": -z, amplitude constraint, +z, phase constraint).  The two plain
+    propagations of each step are compared at the 2e-5 relative-L2 bar; each constraint's output
+    has the required amplitude to 1e-6 and the oracle's phase within 2e-4 rad wherever the
+    propagated value exceeds 1e-3 of its maximum; and the fused ``cwo_gs_run`` after k + 1
+    iterations equals the step-by-step composition bit for bit, so the bar holds for every
+    iterate of the loop itself.  512^2 is a size of Table tbl:gs."""
+    torch, cwo, _ = mods
+    dx, lam, z = 10e-6, 633e-9, 0.1
+    amp, f0 = synth.gs_problem(n, seed=21)
+    a32 = amp.astype(np.float32)
+    plan = cwo.Plan(n, n, dx, dx, lam, z, cwo.ANGULAR)
+    a = torch.from_numpy(a32).cuda()
+    x0 = torch.from_numpy(f0.astype(np.complex64)).cuda()
+
+    def host(t):
+        torch.cuda.synchronize()
+        return t.cpu().numpy().astype(np.complex128)
+
+    def rel(g, w):
+        return float(np.linalg.norm(g - w) / np.linalg.norm(w))
+
+    def constraint_ok(got, want_prop, amp_want):
+        m = np.abs(want_prop)
+        sel = m > 1e-3 * m.max()
+        dph = np.max(np.abs(np.angle(got[sel] * np.conj(want_prop[sel]))))
+        damp = np.max(np.abs(np.abs(got) - amp_want))
+        return dph, damp
+
+    # hologram plane: +z and the phase constraint
+    fwd0 = host(plan.propagate(x0))
+    want0 = oracle.propagate(f0.astype(np.complex64), dx, dx, lam, z)
+    assert rel(fwd0, want0) <= 2e-5
+    u = plan.propagate_epilogue(x0, cwo.EPI_PHASE)
+    dph, damp = constraint_ok(host(u), want0, 1.0)
+    assert dph <= 2e-4 and damp <= 1e-6
+    f = x0.clone()
+    plan.gs_run(a, f, 0, intensity=False)
+    assert torch.equal(f, u)
+    for k in range(iters):
+        uk = host(u)
+        # -z (the adjoint of the +z plan) from the device iterate, then the amplitude constraint
+        back = host(plan.adjoint(u))
+        back_o = oracle.propagate(uk, dx, dx, lam, -z)
+        assert rel(back, back_o) <= 2e-5, f"iteration {k}: back-propagation"
+        obj = plan.propagate_epilogue(u, cwo.EPI_AMPLITUDE, amplitude=a, adjoint=True)
+        dph, damp = constraint_ok(host(obj), back_o, a32.astype(np.float64))
+        assert dph <= 2e-4 and damp <= 1e-6, f"iteration {k}: amplitude constraint {dph:.2e} {damp:.2e}"
+        # +z from the device object field, then the phase constraint
+        fwd = host(plan.propagate(obj))
+        fwd_o = oracle.propagate(host(obj), dx, dx, lam, z)
+        assert rel(fwd, fwd_o) <= 2e-5, f"iteration {k}: forward propagation"
+        u = plan.propagate_epilogue(obj, cwo.EPI_PHASE)
+        dph, damp = constraint_ok(host(u), fwd_o, 1.0)
+        assert dph <= 2e-4 and damp <= 1e-6, f"iteration {k}: phase constraint {dph:.2e} {damp:.2e}"
+        # the fused loop reaches the same iterate
+        f = x0.clone()
+        plan.gs_run(a, f, k + 1, intensity=False)
+        assert torch.equal(f, u), f"iteration {k}: cwo_gs_run differs from the step composition"
+    plan.check()
+    plan.close()
+
+
 def test_gs_batch_equals_single_and_error_drops(mods):
     torch, cwo, gs = mods
     prob = gs.GSProblem(n=256, seed=4, batch=3)
