@@ -40,15 +40,12 @@ __device__ __forceinline__ float2 asm_h_fp32(int kbx, int kby, const HParams& hp
     return make_float2(cs, sn);
 }
 
-// multiply the registers of NV transforms of the same storage column pair (same |kx|) by H
-template <int P, int NV, bool MIXED = false>
-__device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int col, int t, long long item,
-                                        const HParams& hp) {
+// Evaluate the transfer function of storage column `col` at this thread's 16 axis indices
+// e * T + t (DIF order) and hand each value to f(e, h).  The mode and tables are the launch's, or
+// the item's own in a mixed batch.
+template <int P, bool MIXED, class F>
+__device__ __forceinline__ void eval_h(int col, int t, long long item, const HParams& hp, F&& f) {
     constexpr int T = P / 16;
-    auto mul = [&](int e, float2 h) {
-        a[e] = hp.conj ? cmulc(a[e], h) : cmul(a[e], h);
-        if (NV == 2) b[e] = hp.conj ? cmulc(b[e], h) : cmul(b[e], h);
-    };
     int mode = hp.mode;
     float K = 0.f;
     double Kd = hp.K, sx = hp.sx, sy = hp.sy;
@@ -64,7 +61,7 @@ __device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int co
         const int j = abs(__ldg(hp.kbx + col));
         const float2* hc = hp.hcache + (long long)j * hp.hcache_stride + t;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) mul(e, __ldg(hc + e * T));
+        for (int e = 0; e < 16; ++e) f(e, __ldg(hc + e * T));
     } else if (mode == HMODE_FRESNEL) {
         if (MIXED) {
             const float4 X = __ldg(hp.ax + item * hp.x_item_stride + col);
@@ -73,23 +70,23 @@ __device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int co
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const float4 Y = __ldg(hy + e * T);
-                mul(e, cmul(hxc, make_float2(Y.x, Y.y)));
+                f(e, cmul(hxc, make_float2(Y.x, Y.y)));
             }
         } else {
             const float2 hxc = __ldg(hp.hx + item * hp.x_item_stride + col);
             const float2* hy = hp.hy + item * hp.y_item_stride + t;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) mul(e, cmul(hxc, __ldg(hy + e * T)));
+            for (int e = 0; e < 16; ++e) f(e, cmul(hxc, __ldg(hy + e * T)));
         }
     } else if (mode == HMODE_ASM_POLY || mode == HMODE_ASM_EXACT) {
         const float4 X = __ldg(hp.ax + item * hp.x_item_stride + col);
         const float4* ay = hp.ay + item * hp.y_item_stride + t;
         if (mode == HMODE_ASM_POLY) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) mul(e, asm_h_reduced<true>(X, __ldg(ay + e * T), K));
+            for (int e = 0; e < 16; ++e) f(e, asm_h_reduced<true>(X, __ldg(ay + e * T), K));
         } else {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) mul(e, asm_h_reduced<false>(X, __ldg(ay + e * T), K));
+            for (int e = 0; e < 16; ++e) f(e, asm_h_reduced<false>(X, __ldg(ay + e * T), K));
         }
     } else {
         const int kbx = __ldg(hp.kbx + col);
@@ -99,16 +96,27 @@ __device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int co
             for (int e = 0; e < 16; ++e) {
                 const int kby = __ldg(hp.kby + e * T + t);
                 const bool in = inx && kby >= hp.wylo && kby <= hp.wyhi;
-                mul(e, in ? asm_h_fp64_shifted(kbx, kby, Kd, sx, sy, hp.shx, hp.shy) : make_float2(0.f, 0.f));
+                f(e, in ? asm_h_fp64_shifted(kbx, kby, Kd, sx, sy, hp.shx, hp.shy) : make_float2(0.f, 0.f));
             }
             return;
         }
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
             const int kby = __ldg(hp.kby + e * T + t);
-            mul(e, mode == HMODE_ASM_FP32 ? asm_h_fp32(kbx, kby, hp) : asm_h_fp64(kbx, kby, Kd, sx, sy));
+            f(e, mode == HMODE_ASM_FP32 ? asm_h_fp32(kbx, kby, hp) : asm_h_fp64(kbx, kby, Kd, sx, sy));
         }
     }
+}
+
+// multiply the registers of NV transforms of the same storage column pair (same |kx|) by H
+// (by conj(H) for the adjoint)
+template <int P, int NV, bool MIXED = false>
+__device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int col, int t, long long item,
+                                        const HParams& hp) {
+    eval_h<P, MIXED>(col, t, item, hp, [&](int e, float2 h) {
+        a[e] = hp.conj ? cmulc(a[e], h) : cmul(a[e], h);
+        if (NV == 2) b[e] = hp.conj ? cmulc(b[e], h) : cmul(b[e], h);
+    });
 }
 
 // columns per block (single-column kernel) and mirror pairs per block (paired kernel)
@@ -122,7 +130,6 @@ template <int P> constexpr int col_min_blocks() { return (P / 16) * cols_per_blo
 // P = 4096, one 512-thread CTA at P = 8192 (measured 382 us per 4096^2 field vs 488 for the
 // single-column kernel)
 template <int P> constexpr bool col_paired() { return true; }
-
 // single column per transform (used where the paired kernel would not fit in registers)
 template <int P, int C, bool MIXED>
 __global__ void __launch_bounds__(C * (P / 16), col_min_blocks<P>())
@@ -152,20 +159,51 @@ k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restr
 
 // Mirror-pair column kernel: a thread transforms the two storage columns of frequencies +kx and
 // -kx.  H depends on kx only through kx^2 (both methods), so the transfer function is evaluated
-// once for both, and the twiddles of each stage are loaded once for both.
+// (or loaded) once for both, and the twiddles of each stage are loaded once for both.  The
+// exchanges take one barrier each (warp-wide after the first stage) and move a pair's two values
+// at one position with one 128-bit access (P >= 128; P = 8192 keeps 64-bit accesses, which fit in
+// the registers without spilling).  The grid is (items, pair groups), item fastest, so that the
+// CTAs running at one time share few pair groups: the transfer-function values of a pair (the
+// cached table of a once-calculation plan) are read from HBM once and from L2 by the other items.
+// Thread 0 prefetches into L2 the columns of the CTA that will take this CTA's place (`resident`
+// CTAs later in launch order).
+template <int P, int CP>
+constexpr int colp_smem_words() {
+    return (P >= 128 && P < 8192) ? 2 * PairLayout<P, CP>::SLOTS : PadLayout<P, 2 * CP>::WORDS;
+}
+
 template <int P, int CP, bool MIXED>
 __global__ void __launch_bounds__(CP * (P / 16), CP * (P / 16) >= 512 ? 1 : 2)
 k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
-       long long wout_item_stride, const float4* __restrict__ tw, const HParams hp) {
+       long long wout_item_stride, const float4* __restrict__ tw, const HParams hp, int resident) {
     pdl_wait();
     constexpr int T = P / 16, NY = P / 2;
-    using Lay = PadLayout<P, 2 * CP>;
     extern __shared__ float2 sm[];
-    const int t = threadIdx.x % T, cp = threadIdx.x / T;
-    const int j = blockIdx.x * CP + cp;
-    const bool live = j < hp.npairs;               // padding pairs of the last block compute, never store
+    const int t = CP == 1 ? (int)threadIdx.x : (int)threadIdx.x % T;
+    const int cp = CP == 1 ? 0 : (int)threadIdx.x / T;
+    if (threadIdx.x == 0) {
+        const long long nb = (long long)blockIdx.y * gridDim.x + blockIdx.x + resident;
+        if (nb < (long long)gridDim.x * gridDim.y) {
+            const long long itn = nb % gridDim.x;
+            const int gn = (int)(nb / gridDim.x);
+            for (int c = 0; c < CP; ++c) {
+                const int jn = gn * CP + c;
+                if (jn >= hp.npairs) break;
+                const int2 pn = __ldg(hp.pairs + jn);
+                const float2* p0 = win + itn * win_item_stride + (long long)pn.x * NY;
+                const float2* p1 = win + itn * win_item_stride + (long long)pn.y * NY;
+                if ((((uintptr_t)p0 | (uintptr_t)p1) & 15) == 0) {
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p0), "r"(NY * 8) : "memory");
+                    if (pn.y != pn.x)
+                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p1), "r"(NY * 8) : "memory");
+                }
+            }
+        }
+    }
+    const int j = blockIdx.y * CP + cp;
+    const bool live = j < hp.npairs;
     const int2 pr = __ldg(hp.pairs + (live ? j : 0));
-    const long long item = blockIdx.y;
+    const long long item = blockIdx.x;
     const float2* sa = win + item * win_item_stride + (long long)pr.x * NY;
     const float2* sb = win + item * win_item_stride + (long long)pr.y * NY;
     float2 a[16], b[16];
@@ -173,14 +211,21 @@ k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __rest
     for (int e = 0; e < 8; ++e) { a[e] = sa[t + e * T]; b[e] = sb[t + e * T]; }
 #pragma unroll
     for (int e = 8; e < 16; ++e) { a[e] = make_float2(0.f, 0.f); b[e] = make_float2(0.f, 0.f); }
-    fwd2_from<P, 2 * CP, Lay, 0, 8, 0>(a, b, sm, 2 * cp, t, tw);
-    apply_h<P, 2, MIXED>(a, b, pr.x, t, item, hp);
-    inv2_from<P, 2 * CP, Lay, Geo<P>::NST - 1, 0, 0>(a, b, sm, 2 * cp, t, tw);
+    if constexpr (P >= 128 && P < 8192) {
+        fwd2v_from<P, CP, 0, 8>(a, b, reinterpret_cast<float4*>(sm), cp, t, tw);
+        apply_h<P, 2, MIXED>(a, b, pr.x, t, item, hp);
+        inv2v_from<P, CP, Geo<P>::NST - 1>(a, b, reinterpret_cast<float4*>(sm), cp, t, tw);
+    } else {
+        using Lay = PadLayout<P, 2 * CP>;
+        fwd2x_from<P, CP, Lay, 0, 8>(a, b, sm, cp, t, tw);
+        apply_h<P, 2, MIXED>(a, b, pr.x, t, item, hp);
+        inv2x_from<P, CP, Lay, Geo<P>::NST - 1>(a, b, sm, cp, t, tw);
+    }
     if (live) {
         float2* da = wout + item * wout_item_stride + (long long)pr.x * NY;
 #pragma unroll
         for (int e = 0; e < 8; ++e) da[t + e * T] = a[e];
-        if (pr.y != pr.x) {                        // self-mirrored frequencies 0 and Px/2
+        if (pr.y != pr.x) {
             float2* db = wout + item * wout_item_stride + (long long)pr.y * NY;
 #pragma unroll
             for (int e = 0; e < 8; ++e) db[t + e * T] = b[e];
@@ -240,12 +285,13 @@ static cudaError_t col_impl_t(const float2* win, long long win_item_stride, floa
         if (e != cudaSuccess) return e;
     } else if constexpr (col_paired<P>()) {
         constexpr int CP = cols_per_block<P>();
-        const size_t smem = (size_t)PadLayout<P, 2 * CP>::WORDS * sizeof(float2);
-        if ((e = kernel_setup<k_colp<P, CP, MIXED>>(smem, CP * T, nullptr))) return e;
         if (hp.npairs != px / 2 + 1 || !hp.pairs) return cudaErrorInvalidValue;
+        const size_t smem = (size_t)colp_smem_words<P, CP>() * sizeof(float2);
+        int resident = 0;
+        if ((e = kernel_setup<k_colp<P, CP, MIXED>>(smem, CP * T, &resident))) return e;
         const unsigned blocks = (unsigned)((hp.npairs + CP - 1) / CP);
-        e = pdl_launch(k_colp<P, CP, MIXED>, dim3(blocks, items), dim3(CP * T), smem, st, win, win_item_stride, wout,
-                       wout_item_stride, tw, hp);
+        e = pdl_launch(k_colp<P, CP, MIXED>, dim3(items, blocks), dim3(CP * T), smem, st, win, win_item_stride, wout,
+                       wout_item_stride, tw, hp, resident);
         if (e != cudaSuccess) return e;
     } else {
         constexpr int C = cols_per_block<P>();

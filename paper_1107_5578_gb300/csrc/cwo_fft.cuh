@@ -354,6 +354,122 @@ __device__ __forceinline__ void inv2_from(float2 (&a)[16], float2 (&b)[16], floa
     }
 }
 
+// ---- exchanges without trailing barriers
+// The positions a thread reads in one exchange (its positions at the stage being entered) are
+// exactly the positions it writes in the next exchange (it leaves that stage from the same
+// positions), whether the next exchange continues the same transform, turns from the forward to
+// the inverse stages, or starts the next transform.  Every position is read by one thread only,
+// so no thread can overwrite a value another thread has still to read, and each exchange needs a
+// single barrier between its writes and its reads.  The barrier spans only the threads that own
+// one block of the earlier stage: Geo<P>::stride(s) threads for stages s and s + 1, which is the
+// whole transform (T threads) between stages 0 and 1 and at most one warp between later stages.
+// CP transforms pairs of a block use named barriers 1 .. CP when T > 32.
+template <int P, int CP, int S>
+__device__ __forceinline__ void xsync(int cp) {
+    constexpr int G = Geo<P>::stride(S);   // threads sharing one stage-S block
+    if constexpr (G <= 32) {
+        __syncwarp();
+    } else if constexpr (CP == 1) {
+        __syncthreads();
+    } else {
+        static_assert(CP < 16, "named barrier ids");
+        asm volatile("bar.sync %0, %1;" :: "r"(1 + cp), "r"(P / 16) : "memory");
+    }
+}
+
+template <int P, int CP, class Lay, int SW, int SR>
+__device__ __forceinline__ void xch2(float2* __restrict__ sm, int cp, int t, float2 (&a)[16], float2 (&b)[16]) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        sm[Lay::addr(2 * cp, stage_pos<P, SW>(t, e))] = a[e];
+        sm[Lay::addr(2 * cp + 1, stage_pos<P, SW>(t, e))] = b[e];
+    }
+    xsync<P, CP, (SW < SR ? SW : SR)>(cp);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        a[e] = sm[Lay::addr(2 * cp, stage_pos<P, SR>(t, e))];
+        b[e] = sm[Lay::addr(2 * cp + 1, stage_pos<P, SR>(t, e))];
+    }
+}
+
+// Pair layout for xch2v: the values of both transforms of a pair at one position share one
+// 16-byte slot, so an exchange moves them with one 128-bit access each way.  One pad slot per 16
+// positions keeps the eight lanes of every quarter-warp on distinct banks at every stage when a
+// transform has T >= 8 threads (P >= 128).
+template <int P, int CP>
+struct PairLayout {
+    static constexpr int R = P + P / 16;          // slots per pair
+    static constexpr int SLOTS = CP * R;
+    static CWO_HD int slot(int cp, int pos) { return cp * R + pos + (pos >> 4); }
+};
+
+template <int P, int CP, int SW, int SR>
+__device__ __forceinline__ void xch2v(float4* __restrict__ sm, int cp, int t, float2 (&a)[16], float2 (&b)[16]) {
+    using L = PairLayout<P, CP>;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) sm[L::slot(cp, stage_pos<P, SW>(t, e))] = make_float4(a[e].x, a[e].y, b[e].x, b[e].y);
+    xsync<P, CP, (SW < SR ? SW : SR)>(cp);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const float4 v = sm[L::slot(cp, stage_pos<P, SR>(t, e))];
+        a[e] = make_float2(v.x, v.y);
+        b[e] = make_float2(v.z, v.w);
+    }
+}
+
+// forward / inverse stages of a pair with the 128-bit exchange (P >= 128)
+template <int P, int CP, int S, int NZ0>
+__device__ __forceinline__ void fwd2v_from(float2 (&a)[16], float2 (&b)[16], float4* __restrict__ sm, int cp, int t,
+                                           const float4* __restrict__ tw) {
+    using G = Geo<P>;
+    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(a);
+    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(b);
+    if constexpr (S < G::NST - 1) {
+        twiddle2<P, S, false>(a, b, tw, t);
+        xch2v<P, CP, S, S + 1>(sm, cp, t, a, b);
+        fwd2v_from<P, CP, S + 1, NZ0>(a, b, sm, cp, t, tw);
+    }
+}
+
+template <int P, int CP, int S>
+__device__ __forceinline__ void inv2v_from(float2 (&a)[16], float2 (&b)[16], float4* __restrict__ sm, int cp, int t,
+                                           const float4* __restrict__ tw) {
+    using G = Geo<P>;
+    if constexpr (S < G::NST - 1) twiddle2<P, S, true>(a, b, tw, t);
+    stage_butterflies<P, S, true, 16>(a);
+    stage_butterflies<P, S, true, 16>(b);
+    if constexpr (S > 0) {
+        xch2v<P, CP, S, S - 1>(sm, cp, t, a, b);
+        inv2v_from<P, CP, S - 1>(a, b, sm, cp, t, tw);
+    }
+}
+
+template <int P, int CP, class Lay, int S, int NZ0>
+__device__ __forceinline__ void fwd2x_from(float2 (&a)[16], float2 (&b)[16], float2* __restrict__ sm, int cp, int t,
+                                           const float4* __restrict__ tw) {
+    using G = Geo<P>;
+    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(a);
+    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(b);
+    if constexpr (S < G::NST - 1) {
+        twiddle2<P, S, false>(a, b, tw, t);
+        xch2<P, CP, Lay, S, S + 1>(sm, cp, t, a, b);
+        fwd2x_from<P, CP, Lay, S + 1, NZ0>(a, b, sm, cp, t, tw);
+    }
+}
+
+template <int P, int CP, class Lay, int S>
+__device__ __forceinline__ void inv2x_from(float2 (&a)[16], float2 (&b)[16], float2* __restrict__ sm, int cp, int t,
+                                           const float4* __restrict__ tw) {
+    using G = Geo<P>;
+    if constexpr (S < G::NST - 1) twiddle2<P, S, true>(a, b, tw, t);
+    stage_butterflies<P, S, true, 16>(a);
+    stage_butterflies<P, S, true, 16>(b);
+    if constexpr (S > 0) {
+        xch2<P, CP, Lay, S, S - 1>(sm, cp, t, a, b);
+        inv2x_from<P, CP, Lay, S - 1>(a, b, sm, cp, t, tw);
+    }
+}
+
 // forward DIF from stage S to the end; the registers enter holding stage-S input positions
 template <int P, int C, class Lay, int S, int NZ0, int PING, class Tw>
 __device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ sm, int c, int t, const Tw& tw) {
