@@ -228,16 +228,19 @@ def serving_measurement(dev, n_req, rate_hz):
     server.warm_up()
     server.run(serving.make_requests(2000, seed=77, rate_hz=4 * rate_hz))       # warm-up
     reqs = serving.make_requests(n_req, seed=78, rate_hz=rate_hz)
-    server.batches = 0
+    b0 = server.batches
     server.run(reqs)
     cont = serving.latency_stats(reqs)
-    cont["batches"] = server.batches
+    cont["batches"] = server.batches - b0
     cont["mem_peak_bytes"] = server.mem_peak
     plans = {}
     serving.serve_serial(serving.make_requests(400, seed=77, rate_hz=rate_hz), pools, device=dev, plans=plans)
     sreqs = serving.make_requests(n_req, seed=78, rate_hz=rate_hz)
     serving.serve_serial(sreqs, pools, device=dev, plans=plans)
     ser = serving.latency_stats(sreqs)
+    server.close()
+    for v in plans.values():
+        v.close()
     del server, plans, pools
     torch.cuda.empty_cache()
     return {"workload": "mixed_256_to_4096_poisson", "requests": n_req, "rate_hz": rate_hz,
@@ -354,7 +357,8 @@ def main():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=20000, help="0 skips the serving measurement")
+    ap.add_argument("--serving-requests", type=int, default=100000,
+                    help="requests of the mixed-size serving stream (0 skips the serving measurements)")
     ap.add_argument("--serving-rate", type=float, default=2000.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -463,7 +467,7 @@ def main():
     gs_res = gs_measurement(dev) if rank == 0 else None
     serve = serving_measurement(dev, args.serving_requests, args.serving_rate) \
         if args.serving_requests > 0 and rank == 0 else None
-    serve_high = serving_measurement(dev, args.serving_requests, 4 * args.serving_rate) \
+    serve_high = serving_measurement(dev, min(args.serving_requests, 20000), 4 * args.serving_rate) \
         if args.serving_requests > 0 and rank == 0 else None
     if world > 1:
         dist.destroy_process_group()

@@ -129,6 +129,15 @@ cudaError_t launch_fourier_rows(int px, const float2* in, long long in_item_stri
 cudaError_t launch_fourier_cols(int py, const float2* win, long long win_item_stride, float2* out, long long out_item_stride,
                                 int nx, int items, const int* st_of_col, const int* row_of_idx, const float2* post_x,
                                 const float2* post_y, const float4* tw, cudaStream_t st);
+// copy `fields` (<= kCopyMaxFields) fields of `elems` complex64 values from list.src[i] to
+// list.dst[i] (device addresses; a NULL address skips item i) -- the serving runtime's gather
+// and scatter
+constexpr int kCopyMaxFields = 64;
+struct CopyList {
+    const float2* src[kCopyMaxFields];
+    float2* dst[kCopyMaxFields];
+};
+cudaError_t launch_copy_fields(const CopyList& list, int fields, long long elems, cudaStream_t st);
 // Encode the tensor map of an intermediate [cap][px][ny] at base (host only; no allocation).
 cudaError_t make_intermediate_map(CUtensorMap* map, void* base, int ny, int px, int cap, int rows);
 cudaError_t launch_col(int py, const float2* win, long long win_item_stride, float2* wout,

@@ -1,23 +1,25 @@
 """Serving: continuous batching of mixed-size diffraction requests on one GPU.
 
-Requests carry their own field size N, type (ASM / Fresnel), distance, wavelength and pitch.
-The server keeps, per size, a few slots -- a plan (tables and scratch resident), a CUDA stream and
+Requests carry their own field size N, type (ASM / Fresnel), distance, wavelength and pitch.  The
+scheduling runtime is native (include/cwo_serve.h): per size it keeps a few slots -- a plan
+(tables and scratch resident), a CUDA stream (higher priority for small sizes), an event and
 input/output buffers -- and a queue.  Whenever a slot of a size is free and the device-memory
 budget admits the batch, the pending requests of that size (up to the slot's capacity) are
-gathered into the slot's input buffer and propagated in one mixed batch (cwo_propagate_items:
-one set of three launches for the whole batch, each item with its own parameters).  Requests that
-arrive while others are on the GPU are admitted as soon as a slot and memory free up, and batches
-of different sizes run concurrently on different streams (small sizes on higher-priority
-streams), so short requests do not queue behind large ones.  Completion is observed by polling
-the slot's event; latency is arrival -> observed completion on the host clock.
+gathered into the slot's input buffer and propagated in one mixed batch (cwo_propagate_items: one
+set of launches for the whole batch, each item with its own parameters).  Requests that arrive
+while others are on the GPU are admitted as soon as a slot and memory free up, and batches of
+different sizes run concurrently on different streams, so short requests do not queue behind
+large ones.  Completion is observed by polling the slots' events; latency is arrival -> observed
+completion on the host clock.  This module marshals requests and results; every scheduling
+decision is taken by the runtime.
 
-The baseline (``serve_serial``) propagates the same requests one at a time in arrival order.
+The baseline (``serve_serial``) propagates the same requests one at a time in arrival order,
+also natively (cwo_server_run_serial).
 """
 from __future__ import annotations
 
-import collections
+import ctypes
 import dataclasses
-import time
 
 import numpy as np
 import torch
@@ -40,6 +42,7 @@ class Request:
     field: torch.Tensor | None = None  # or an explicit [n, n] complex64 CUDA field
     t_done: float | None = None
     result: torch.Tensor | None = None
+    ticket: int = -1
 
     def done(self) -> bool:
         return self.t_done is not None
@@ -48,9 +51,50 @@ class Request:
         return {"type": self.kind, "z": self.z, "wavelength": self.wavelength, "dx": self.pitch, "dy": self.pitch}
 
 
+# cwo_request of include/cwo_serve.h
+REQUEST_DTYPE = np.dtype([("n", "<i4"), ("type", "<i4"), ("z", "<f8"), ("wavelength", "<f8"), ("pitch", "<f8"),
+                          ("field", "<u8"), ("out", "<u8"), ("t_arrival", "<f8")], align=True)
+assert REQUEST_DTYPE.itemsize == 56
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("mem_in_use", ctypes.c_size_t),
+                ("mem_peak", ctypes.c_size_t), ("mem_budget", ctypes.c_size_t)]
+
+
+_SIGS = {
+    "cwo_server_create": ([ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t,
+                           ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "cwo_server_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "cwo_server_batch_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "cwo_server_admit": ([ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int,
+                          ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cwo_server_submit": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+    "cwo_server_after": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "cwo_server_step": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cwo_server_done": ([ctypes.c_void_p, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "cwo_server_run": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "cwo_server_run_serial": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "cwo_server_warm_up": ([ctypes.c_void_p], ctypes.c_int),
+    "cwo_server_get_stats": ([ctypes.c_void_p, ctypes.POINTER(_Stats)], ctypes.c_int),
+}
+
+
+def _lib():
+    L = cwo.lib()
+    if not getattr(L, "_cwo_serve_bound", False):
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        L._cwo_serve_bound = True
+    return L
+
+
 def validate(req: Request) -> None:
-    """Host-side admission check; raises ValueError without touching the device."""
-    if req.n not in DEFAULT_MAX_BATCH and not (16 <= req.n <= 4096 and (req.n & (req.n - 1)) == 0):
+    """Host-side argument check of one request (the runtime checks again, with the device
+    pointers); raises ValueError without touching the device."""
+    if not (16 <= req.n <= 4096 and (req.n & (req.n - 1)) == 0):
         raise ValueError(f"request {req.rid}: unsupported size {req.n}")
     if req.kind not in (cwo.ANGULAR, cwo.FRESNEL_CONV):
         raise ValueError(f"request {req.rid}: unsupported type {req.kind}")
@@ -62,35 +106,18 @@ def validate(req: Request) -> None:
 
 def batch_bytes(n: int, b: int) -> int:
     """Device bytes a batch of b fields of n x n occupies while in flight (scratch + in + out)."""
-    return cwo.device_bytes(n, n, b) + 2 * b * n * n * 8
+    out = ctypes.c_size_t(0)
+    cwo.check(_lib().cwo_server_batch_bytes(int(n), int(b), ctypes.byref(out)), "cwo_server_batch_bytes")
+    return int(out.value)
 
 
-def admit(queued: int, capacity: int, in_use: int, budget: int, bytes_of) -> int:
-    """How many of `queued` requests one free slot takes now: up to its capacity, halved until
-    the batch fits the memory budget next to what is in flight (0: wait for completions)."""
-    b = min(queued, capacity)
-    while b > 0 and in_use + bytes_of(b) > budget:
-        b //= 2
-    return b
-
-
-class _Slot:
-    def __init__(self, n, capacity, device, priority):
-        self.n, self.capacity = n, capacity
-        self.plan = cwo.Plan(n, n, cwo.DEFAULT_PITCH, None, cwo.DEFAULT_WAVELENGTH, 0.1, cwo.ANGULAR)
-        self.plan.reserve(capacity)
-        self.stream = torch.cuda.Stream(device=device, priority=priority)
-        self.inbuf = torch.empty((capacity, n, n), dtype=torch.complex64, device=device)
-        self.outbuf = torch.empty_like(self.inbuf)
-        self.event = torch.cuda.Event()
-        self.idx_host = torch.empty(capacity, dtype=torch.int64).pin_memory()
-        self.idx_dev = torch.empty(capacity, dtype=torch.int64, device=device)
-        self.reqs: list[Request] = []
-        self.bytes = 0
-
-    @property
-    def busy(self):
-        return bool(self.reqs)
+def admit(queued: int, capacity: int, in_use: int, budget: int, n: int) -> int:
+    """How many of `queued` requests of size n one free slot takes now (the runtime's rule: up to
+    its capacity, halved until the batch fits the memory budget next to what is in flight)."""
+    out = ctypes.c_int(0)
+    cwo.check(_lib().cwo_server_admit(int(queued), int(capacity), int(in_use), int(budget), int(n), ctypes.byref(out)),
+              "cwo_server_admit")
+    return int(out.value)
 
 
 class Server:
@@ -101,28 +128,80 @@ class Server:
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.max_batch = dict(DEFAULT_MAX_BATCH if max_batch is None else max_batch)
         self.sizes = sorted(sizes)
-        self.slots = {}
-        for n in self.sizes:
-            prio = -1 if n <= 512 else 0            # short requests on high-priority streams
-            self.slots[n] = [_Slot(n, self.max_batch[n], self.device, prio) for _ in range(slots_per_size)]
-        self.queues = {n: collections.deque() for n in self.sizes}
-        self.mem_budget = mem_budget if mem_budget is not None else sum(
-            batch_bytes(n, self.max_batch[n]) * slots_per_size for n in self.sizes)
-        self.mem_in_use = 0
-        self.mem_peak = 0
         self.pools = pools or {}
         self.keep_results = keep_results
-        self.batches = 0
+        self._handle = ctypes.c_void_p()
+        sz = (ctypes.c_int * len(self.sizes))(*self.sizes)
+        mb = (ctypes.c_int * len(self.sizes))(*[self.max_batch[n] for n in self.sizes])
+        with torch.cuda.device(self.device):
+            cwo.check(_lib().cwo_server_create(len(self.sizes), sz, mb, int(slots_per_size), int(mem_budget or 0),
+                                               ctypes.byref(self._handle)), "cwo_server_create")
+        self._pending: dict[int, Request] = {}
         self._next_rid = 1 << 40
+
+    def close(self) -> None:
+        if self._handle:
+            _lib().cwo_server_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stats(self) -> _Stats:
+        st = _Stats()
+        cwo.check(_lib().cwo_server_get_stats(self._handle, ctypes.byref(st)), "cwo_server_get_stats")
+        return st
+
+    @property
+    def batches(self) -> int:
+        return int(self._stats().batches)
+
+    @property
+    def mem_peak(self) -> int:
+        return int(self._stats().mem_peak)
+
+    @property
+    def mem_budget(self) -> int:
+        return int(self._stats().mem_budget)
+
+    @property
+    def mem_in_use(self) -> int:
+        return int(self._stats().mem_in_use)
+
+    def _fill(self, rec, r: Request) -> None:
+        validate(r)
+        if r.field is not None:
+            src = r.field
+        else:
+            pool = self.pools[r.n]
+            src = pool[r.pool_index % pool.shape[0]]
+        if self.keep_results:
+            r.result = torch.empty((r.n, r.n), dtype=torch.complex64, device=self.device)
+        rec["n"], rec["type"], rec["z"] = r.n, r.kind, r.z
+        rec["wavelength"], rec["pitch"] = r.wavelength, r.pitch
+        rec["field"] = src.data_ptr()
+        rec["out"] = r.result.data_ptr() if r.result is not None else 0
+        rec["t_arrival"] = r.t_arrival
 
     def submit(self, req: Request) -> Request:
         """Queue a request; the returned object is its future (done(), result after completion)."""
-        validate(req)
-        if req.n not in self.queues:
+        if req.n not in self.sizes:
             raise ValueError(f"request {req.rid}: size {req.n} is not served")
-        if batch_bytes(req.n, 1) > self.mem_budget:
-            raise ValueError(f"request {req.rid}: one {req.n}^2 field needs more than the memory budget")
-        self.queues[req.n].append(req)
+        rec = np.zeros(1, dtype=REQUEST_DTYPE)
+        self._fill(rec[0], req)
+        if req.field is not None:                   # caller-made field: order after its producer
+            cwo.check(_lib().cwo_server_after(self._handle, torch.cuda.current_stream(self.device).cuda_stream),
+                      "cwo_server_after")
+        t = ctypes.c_longlong(-1)
+        st = _lib().cwo_server_submit(self._handle, rec.ctypes.data, ctypes.byref(t))
+        if st == cwo.ERR_INVALID_ARG:
+            raise ValueError(f"request {req.rid}: {cwo.last_error()}")
+        cwo.check(st, "cwo_server_submit")
+        req.ticket = int(t.value)
+        self._pending[req.ticket] = req
         return req
 
     def submit_field(self, field: torch.Tensor, z: float, wavelength: float = cwo.DEFAULT_WAVELENGTH,
@@ -132,13 +211,18 @@ class Server:
                 or field.device != self.device:
             raise ValueError("field must be a square complex64 tensor on the server's device")
         self._next_rid += 1
-        req = Request(self._next_rid, int(field.shape[0]), kind, z, wavelength, pitch, field=field)
+        req = Request(self._next_rid, int(field.shape[0]), kind, z, wavelength, pitch, field=field.contiguous())
         return self.submit(req)
 
-    def step(self, now: float | None = None) -> int:
+    def step(self) -> int:
         """Admit what fits and collect what finished; returns the number of completions."""
-        self.dispatch()
-        return self.poll(time.perf_counter() if now is None else now)
+        c = ctypes.c_int(0)
+        cwo.check(_lib().cwo_server_step(self._handle, ctypes.byref(c)), "cwo_server_step")
+        if c.value:
+            t = ctypes.c_double(0.0)
+            for k in [k for k in self._pending if _lib().cwo_server_done(self._handle, k, ctypes.byref(t)) == 1]:
+                self._pending.pop(k).t_done = t.value
+        return int(c.value)
 
     def wait(self, req: Request) -> torch.Tensor | None:
         """Drive the server until `req` completes; returns its result when results are kept."""
@@ -147,148 +231,52 @@ class Server:
         return req.result
 
     def pending(self) -> int:
-        return sum(len(q) for q in self.queues.values()) + sum(len(s.reqs) for v in self.slots.values() for s in v)
-
-    def poll(self, now: float) -> int:
-        done = 0
-        for n in self.sizes:
-            for s in self.slots[n]:
-                if s.reqs and s.event.query():
-                    for i, r in enumerate(s.reqs):
-                        r.t_done = now
-                        if self.keep_results:
-                            r.result = s.outbuf[i].clone()
-                    done += len(s.reqs)
-                    s.reqs = []
-                    self.mem_in_use -= s.bytes
-                    s.bytes = 0
-        return done
-
-    def dispatch(self) -> None:
-        for n in self.sizes:                        # smallest first
-            q = self.queues[n]
-            for s in self.slots[n]:
-                if not q:
-                    break
-                if s.busy:
-                    continue
-                b = admit(len(q), s.capacity, self.mem_in_use, self.mem_budget, lambda k: batch_bytes(n, k))
-                if b == 0:
-                    break                           # retried after completions free memory
-                need = batch_bytes(n, b)
-                reqs = [q.popleft() for _ in range(b)]
-                self._launch(s, reqs)
-                self.mem_in_use += need
-                self.mem_peak = max(self.mem_peak, self.mem_in_use)
-                s.bytes = need
-
-    def _launch(self, s: _Slot, reqs: list[Request]) -> None:
-        b = len(reqs)
-        if any(r.field is not None for r in reqs):  # caller-made fields: order after their producer
-            s.stream.wait_stream(torch.cuda.current_stream(self.device))
-        with torch.cuda.stream(s.stream):
-            if b == 1:                              # no gather: propagate straight from the source
-                r = reqs[0]
-                if r.field is not None:
-                    x = r.field.unsqueeze(0)
-                else:
-                    pool = self.pools[s.n]
-                    k = r.pool_index % pool.shape[0]
-                    x = pool[k:k + 1]
-            elif all(r.field is None for r in reqs):
-                pool = self.pools[s.n]
-                s.idx_host[:b].copy_(torch.tensor([r.pool_index % pool.shape[0] for r in reqs]))
-                s.idx_dev[:b].copy_(s.idx_host[:b], non_blocking=True)
-                torch.index_select(pool, 0, s.idx_dev[:b], out=s.inbuf[:b])
-                x = s.inbuf[:b]
-            else:
-                for i, r in enumerate(reqs):
-                    s.inbuf[i].copy_(r.field if r.field is not None else self.pools[s.n][r.pool_index])
-                x = s.inbuf[:b]
-            s.plan.propagate_items(x, [r.item() for r in reqs], out=s.outbuf[:b], stream=s.stream)
-            s.event.record(s.stream)
-        s.reqs = reqs
-        self.batches += 1
+        return len(self._pending)
 
     def warm_up(self) -> None:
-        """Touch every code path a run takes (single and gathered batches of every size) so that
-        no first-use cost (module loading, allocator growth) lands inside a measured run."""
-        for n in self.sizes:
-            pool = self.pools.get(n)
-            if pool is None:
-                continue
-            for s in self.slots[n]:
-                for b in (1, min(2, s.capacity)):
-                    for kind in (cwo.ANGULAR, cwo.FRESNEL_CONV):
-                        reqs = [Request(-1, n, kind, 0.1, 532e-9, 8e-6, pool_index=k) for k in range(b)]
-                        self._launch(s, reqs)
-                        s.event.synchronize()
-                        s.reqs = []
-        self.batches = 0
+        """Touch every path a run takes (single and gathered batches of every size and type) so
+        that no first-use cost lands inside a measured run."""
+        cwo.check(_lib().cwo_server_warm_up(self._handle), "cwo_server_warm_up")
 
     def run(self, requests: list[Request]) -> float:
-        """Open-loop run: requests are released at their arrival times (seconds from start).
-        Python's cyclic garbage collector is paused for the run (a collection over a large heap
-        would stall the loop for its duration)."""
-        import gc
-        requests = sorted(requests, key=lambda r: r.t_arrival)
-        gc.collect()
-        was_enabled = gc.isenabled()
-        gc.disable()
-        try:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            i, total, done = 0, len(requests), 0
-            while done < total:
-                now = time.perf_counter() - t0
-                while i < total and requests[i].t_arrival <= now:
-                    self.submit(requests[i])
-                    i += 1
-                self.dispatch()
-                done += self.poll(time.perf_counter() - t0)
-            return time.perf_counter() - t0
-        finally:
-            if was_enabled:
-                gc.enable()
+        """Open-loop run: requests are released at their arrival times (seconds from start) and
+        scheduled by the runtime; sets each request's t_done; returns the makespan."""
+        recs = np.zeros(len(requests), dtype=REQUEST_DTYPE)
+        for rec, r in zip(recs, requests):
+            self._fill(rec, r)
+        t_done = np.zeros(len(requests), dtype=np.float64)
+        st = _lib().cwo_server_run(self._handle, recs.ctypes.data, len(requests), t_done.ctypes.data)
+        if st == cwo.ERR_INVALID_ARG:
+            raise ValueError(cwo.last_error())
+        cwo.check(st, "cwo_server_run")
+        for r, t in zip(requests, t_done):
+            r.t_done = float(t)
+        return float(t_done.max()) if len(requests) else 0.0
 
 
 def serve_serial(requests: list[Request], pools, device="cuda", keep_results=False, plans=None) -> float:
     """Baseline: one request at a time in arrival order, each propagated alone and waited for
-    (garbage collector paused as in Server.run)."""
-    import gc
-    gc.collect()
-    was_enabled = gc.isenabled()
-    gc.disable()
-    try:
-        return _serve_serial(requests, pools, device, keep_results, plans)
-    finally:
-        if was_enabled:
-            gc.enable()
-
-
-def _serve_serial(requests, pools, device, keep_results, plans) -> float:
-    requests = sorted(requests, key=lambda r: r.t_arrival)
-    dev = torch.device(device)
-    plans = {} if plans is None else plans
-    outs = {}
-    stream = torch.cuda.Stream(device=dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for r in requests:
-        if r.n not in plans:
-            plans[r.n] = cwo.Plan(r.n, r.n, cwo.DEFAULT_PITCH, None, cwo.DEFAULT_WAVELENGTH, 0.1, cwo.ANGULAR)
-            outs[r.n] = torch.empty((1, r.n, r.n), dtype=torch.complex64, device=dev)
-        if r.n not in outs:
-            outs[r.n] = torch.empty((1, r.n, r.n), dtype=torch.complex64, device=dev)
-        while time.perf_counter() - t0 < r.t_arrival:
-            pass
-        x = (r.field if r.field is not None else pools[r.n][r.pool_index % pools[r.n].shape[0]]).unsqueeze(0)
-        plans[r.n].propagate_items(x, [r.item()], out=outs[r.n], stream=stream)
-        stream.synchronize()
-        r.t_done = time.perf_counter() - t0
-        if keep_results:
-            r.result = outs[r.n][0].clone()
-    return time.perf_counter() - t0
+    (native, cwo_server_run_serial).  ``plans``: a dict in which the baseline keeps its server
+    between calls (so that a warm-up call leaves it ready)."""
+    sizes = sorted({r.n for r in requests} | set(pools.keys()))
+    cache = {} if plans is None else plans
+    key = ("serial", tuple(sizes), bool(keep_results))
+    srv = cache.get(key)
+    if srv is None:
+        srv = Server(sizes=sizes, max_batch={n: 1 for n in sizes}, slots_per_size=1, device=device, pools=pools,
+                     keep_results=keep_results)
+        srv.warm_up()
+        cache[key] = srv
+    srv.pools = pools
+    recs = np.zeros(len(requests), dtype=REQUEST_DTYPE)
+    for rec, r in zip(recs, requests):
+        srv._fill(rec, r)
+    t_done = np.zeros(len(requests), dtype=np.float64)
+    cwo.check(_lib().cwo_server_run_serial(srv._handle, recs.ctypes.data, len(requests), t_done.ctypes.data),
+              "cwo_server_run_serial")
+    for r, t in zip(requests, t_done):
+        r.t_done = float(t)
+    return float(t_done.max()) if len(requests) else 0.0
 
 
 def make_pools(sizes, per_size=4, device="cuda", seed=100):

@@ -36,15 +36,26 @@ def test_validation_rejects_bad_requests_without_a_device():
 
 
 def test_admission_by_memory_budget():
+    """The runtime's admission rule (cwo_server_admit, host only): up to the slot's capacity and
+    the queue, halved until the batch fits the budget next to the bytes in flight."""
     pytest.importorskip("torch")
-    from paper_1107_5578_gb300 import serving
-    per = lambda k: 100 * k                                   # bytes of a batch of k
-    assert serving.admit(10, 8, 0, 10_000, per) == 8            # capacity bound
-    assert serving.admit(3, 8, 0, 10_000, per) == 3             # queue bound
-    assert serving.admit(8, 8, 9_500, 10_000, per) == 4         # halved to fit: 9500 + 400 <= 10000
-    assert serving.admit(8, 8, 9_950, 10_000, per) == 0         # nothing fits: wait for completions
-    assert serving.admit(0, 8, 0, 10_000, per) == 0
-    for q in range(0, 20):
-        for used in range(0, 10_001, 250):
-            b = serving.admit(q, 8, used, 10_000, per)
-            assert 0 <= b <= min(q, 8) and (b == 0 or used + per(b) <= 10_000)
+    from paper_1107_5578_gb300 import build, serving
+    build.build()
+    n = 256
+    per = {k: serving.batch_bytes(n, k) for k in range(1, 9)}
+    assert all(per[k + 1] > per[k] for k in range(1, 8))          # bytes grow with the batch
+    assert per[1] > 2 * n * n * 8                                 # plan scratch + input + output
+    big = 10 * per[8]
+    assert serving.admit(10, 8, 0, big, n) == 8                   # capacity bound
+    assert serving.admit(3, 8, 0, big, n) == 3                    # queue bound
+    assert serving.admit(8, 8, big - per[4], big, n) == 4         # halved to fit
+    assert serving.admit(8, 8, big - per[1] + 1, big, n) == 0     # nothing fits: wait for completions
+    assert serving.admit(0, 8, 0, big, n) == 0
+    for q in range(0, 12):
+        for used in range(0, big + 1, big // 17):
+            b = serving.admit(q, 8, used, big, n)
+            assert 0 <= b <= min(q, 8) and (b == 0 or used + per[b] <= big)
+            c = min(q, 8)                                         # the first fit of c, c // 2, ...
+            while c > 0 and used + per[c] > big:
+                c //= 2
+            assert b == c
