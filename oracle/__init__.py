@@ -87,6 +87,8 @@ def _load():
             lib.orc_propagate_direct.restype = I
             lib.orc_max_threads.argtypes = []
             lib.orc_max_threads.restype = I
+            lib.orc_set_threads.argtypes = [I]
+            lib.orc_set_threads.restype = None
             _lib = lib
     return _lib
 
@@ -98,6 +100,11 @@ def _c128(a) -> np.ndarray:
 def max_threads() -> int:
     """OpenMP threads the oracle's parallel loops use."""
     return int(_load().orc_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's parallel loops from now on (timing; results do not depend on it)."""
+    _load().orc_set_threads(int(n))
 
 
 def dft(x, sign: int = -1) -> np.ndarray:

@@ -58,6 +58,16 @@ int orc_max_threads(void) {
 #endif
 }
 
+/* Threads of the parallel loops that follow (timing only: each row or column transform is
+ * computed by one thread in the same order whatever the count, so results do not depend on it). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 static int is_pow2(long n) { return n >= 1 && (n & (n - 1)) == 0; }
 
 /* Signed bin index on a grid of n points: k for k < n/2, k - n otherwise.  Bin n/2 (Nyquist)

@@ -460,3 +460,17 @@ def test_shifted_fresnel_gaussian_off_axis():
     y, x = np.mgrid[0:n, 0:n].astype(float)
     r2 = ((x - n / 2) * p1 + ox1) ** 2 + ((y - n / 2) * p1 + oy1) ** 2
     assert np.max(np.abs(out - _fresnel_gaussian(r2, w0, z))) < 1e-10
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    """Timing runs the oracle on one thread and on all of them; the arithmetic is the same."""
+    u = synth.random_field(64, seed=31)
+    cores = oracle.max_threads()
+    try:
+        oracle.set_threads(1)
+        one = oracle.propagate(u, 10e-6, 10e-6, 633e-9, 0.05, oracle.ANGULAR)
+        oracle.set_threads(max(2, cores))
+        many = oracle.propagate(u, 10e-6, 10e-6, 633e-9, 0.05, oracle.ANGULAR)
+    finally:
+        oracle.set_threads(cores)
+    assert np.array_equal(one, many)
