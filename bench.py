@@ -121,6 +121,231 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ---- FP32 arithmetic of the passes, counted from the kernels' own butterflies (P = 4096: three
+# radix-16 DIF stages).  FP32 instructions per 16 points: a radix-16 butterfly done as 4 x 4
+# (eight radix-4 DFTs of 16 additions, eight non-trivial inner twiddles of 4 instructions) = 160;
+# the first forward stage, whose upper 8 inputs are the zero padding, 128; the last inverse stage,
+# of which only the lower 8 outputs are kept, 144; the 15 inter-stage twiddle multiplications
+# (complex multiply = 2 FMUL + 2 FFMA) 60.  ncu counts of the same kernels (fadd + fmul + ffma
+# thread instructions) agree within 4% (profiles/asm_2048_kernels_full.md).
+FP32_R16, FP32_R16_ZERO_HALF_IN, FP32_R16_HALF_OUT, FP32_TWIDDLES = 160, 128, 144, 60
+FP32_FWD = (FP32_R16_ZERO_HALF_IN + FP32_TWIDDLES + FP32_R16 + FP32_TWIDDLES + FP32_R16) / 16.0   # per point
+FP32_INV = (FP32_R16 + FP32_TWIDDLES + FP32_R16 + FP32_TWIDDLES + FP32_R16_HALF_OUT) / 16.0       # per point
+FP32_PER_PASS = {   # FP32 instructions per propagation of an N x N field (P = 2N)
+    "row_fwd": FP32_FWD * N * 2 * N,                      # N rows of P points
+    "col_fwd_h_inv": (FP32_FWD + 4.0 + FP32_INV) * (2 * N) ** 2,   # P columns: FFT, x H (loaded), IFFT
+    "row_inv": (FP32_INV + 1.0) * N * 2 * N,              # N rows: IFFT, 1/(Px Py) on the kept half
+}
+
+
+def fp32_peak(dev):
+    """FP32 instruction rate of this GPU (instructions/s): sixteen independent FFMA chains per
+    thread, 32 warps per SM, timed with CUDA events, best of 5 (cwo_debug_ffma_rate)."""
+    import torch
+    from paper_1107_5578_gb300 import cwo
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = sms * 8, 2048
+    out = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    L = cwo.lib()
+    stream = torch.cuda.current_stream()
+    best = float("inf")
+    for k in range(6):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cwo.check(L.cwo_debug_ffma_rate(blocks, iters, out.data_ptr(), stream.cuda_stream), "cwo_debug_ffma_rate")
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            best = min(best, a.elapsed_time(b) / 1e3)
+    return blocks * 256 * iters * 16 / best
+
+
+class NvmlClockSampler:
+    """SM clock and throttle reasons sampled every 2 ms by NVML queries (read only) during the
+    timed region; falls back to the nvidia-smi sampler where NVML cannot be loaded."""
+    BITS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown", 0x4: "sw_power_cap"}
+
+    def __init__(self, torch_index: int):
+        self.index = torch_index
+        self.fallback = None
+        self.samples = []
+
+    def _handle(self):
+        import ctypes
+        import torch
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        props = torch.cuda.get_device_properties(self.index)
+        uuid = getattr(props, "uuid", None)
+        ok = False
+        if uuid is not None:
+            u = str(uuid)
+            u = u if u.startswith("GPU-") else "GPU-" + u
+            ok = nv.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)) == 0
+        if not ok:
+            bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+            ok = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) == 0
+        if not ok:
+            raise OSError("no NVML handle for the device")
+        return nv, h
+
+    def __enter__(self):
+        import ctypes
+        import threading
+        try:
+            nv, h = self._handle()
+        except Exception:
+            self.fallback = ClockSampler(self.index).__enter__()
+            return self
+        reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint(0)
+        nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+        self.max_mhz = float(mx.value)
+        self.stop = threading.Event()
+
+        def run():
+            clk, rs = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+            while not self.stop.is_set():
+                if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and reasons_fn(h, ctypes.byref(rs)) == 0:
+                    self.samples.append((float(clk.value), int(rs.value)))
+                time.sleep(0.002)
+
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
+        t0 = time.perf_counter()
+        while not self.samples and time.perf_counter() - t0 < 1.0:
+            time.sleep(0.001)
+        self.skip = len(self.samples)
+        return self
+
+    def __exit__(self, *a):
+        if self.fallback is not None:
+            return self.fallback.__exit__(*a)
+        self.stop.set()
+        self.thread.join(timeout=2)
+
+    def summary(self):
+        if self.fallback is not None:
+            return self.fallback.summary()
+        rows = self.samples[self.skip:] or self.samples[-1:]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        reasons = sorted({name for _, r in rows for bit, name in self.BITS.items() if r & bit})
+        return {"sm_mhz": float(np.median([c for c, _ in rows])), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(rows), "sampler": "nvml, 2 ms"}
+
+
+def oracle_times(fn, reps=2):
+    """Seconds per call of fn() with the oracle on one thread and on all of them."""
+    import oracle
+    cores = oracle.max_threads()
+    out = {}
+    for label, th in (("1_thread", 1), (f"{cores}_threads", cores)):
+        oracle.set_threads(th)
+        fn()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        out[label] = round((time.perf_counter() - t0) / reps, 4)
+    oracle.set_threads(cores)
+    return out, cores
+
+
+def rel_l2(got, want):
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+
+def config_asm_512(dev, steps=200):
+    """512^2 ASM (633 nm, 10 um, z = 0.05 m, padded to 1024^2) from a complex128 field: relative
+    L2 against the FP64 oracle, device throughput as a batch of 64 and one propagation at a time,
+    and the oracle's time on 1 and all host threads."""
+    import torch
+    import oracle
+    from paper_1107_5578_gb300 import cwo, synth
+    n, z = 512, 0.05
+    u = synth.random_field(n, seed=1)
+    plan = cwo.Plan(n, n, PITCH, PITCH, LAM, z, cwo.ANGULAR)
+    plan.reserve(64)
+    x1 = torch.from_numpy(u.astype(np.complex64)).to(dev)
+    got = plan.propagate(x1).cpu().numpy().astype(np.complex128)
+    want = oracle.propagate(u, PITCH, PITCH, LAM, z, oracle.ANGULAR)
+    xb = torch.from_numpy(np.stack([synth.random_field(n, seed=10 + k) for k in range(64)]).astype(np.complex64)).to(dev)
+    yb = torch.empty_like(xb)
+    y1 = torch.empty_like(x1)
+
+    def timed(f, reps):
+        for _ in range(5):
+            f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            f()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms_b = timed(lambda: plan.propagate_batch(xb, out=yb), steps)
+    ms_1 = timed(lambda: plan.propagate(x1, out=y1), steps)
+    plan.close()
+    ot, cores = oracle_times(lambda: oracle.propagate(u, PITCH, PITCH, LAM, z, oracle.ANGULAR), reps=3)
+    return {"workload": "asm_512_pad1024", "rel_l2_vs_oracle": rel_l2(got, want),
+            "batch64_propagations_per_s": round(64 / (ms_b / 1e3), 1), "single_us": round(1e3 * ms_1, 2),
+            "single_propagations_per_s": round(1 / (ms_1 / 1e3), 1),
+            "oracle_s_per_propagation": ot, "oracle_cores": cores}
+
+
+def config_fresnel_stack_errors(dev):
+    """The 16-plane Fresnel stack of 2048^2 (one call): planes 0, 7 and 15 against the FP64 oracle
+    propagating the same source to the same distance, and the oracle's time per plane."""
+    import torch
+    import oracle
+    from paper_1107_5578_gb300 import cwo, synth
+    n, planes = 2048, 16
+    zs = [float(v) for v in np.linspace(0.1, 0.4, planes)]
+    u = synth.masked_gaussian(n, seed=2)
+    plan = cwo.Plan(n, n, 8e-6, 8e-6, 532e-9, zs[0], cwo.FRESNEL_CONV)
+    y = plan.propagate_stack(torch.from_numpy(u.astype(np.complex64)).to(dev), zs)
+    torch.cuda.synchronize()
+    errs = {}
+    for j in (0, 7, 15):
+        want = oracle.propagate(u.astype(np.complex64), 8e-6, 8e-6, 532e-9, zs[j], oracle.FRESNEL_CONV)
+        errs[f"plane_{j}_z_{zs[j]:.3f}"] = rel_l2(y[j].cpu().numpy().astype(np.complex128), want)
+    plan.close()
+    ot, cores = oracle_times(lambda: oracle.propagate(u, 8e-6, 8e-6, 532e-9, zs[7], oracle.FRESNEL_CONV), reps=1)
+    return {"rel_l2_vs_oracle": errs, "oracle_s_per_plane": ot, "oracle_cores": cores}
+
+
+def config_precision_4096(dev):
+    """Precision study at 4096^2 (padded to 8192^2; unit amplitude, random phase; 532 nm, 3.74 um):
+    relative L2 and the largest wrapped phase error (|U| > 1e-3 max |U|) of the three
+    transfer-function phase arms against the FP64 oracle, for z = 0.05, 0.2 and 1.0 m."""
+    import oracle
+    from paper_1107_5578_gb300 import precision, synth
+    n, lam, pitch = 4096, 532e-9, 3.74e-6
+    u = synth.random_phase_field(n, seed=3).astype(np.complex64)
+    out = {}
+    for z in (0.05, 0.2, 1.0):
+        ref = oracle.propagate(u, pitch, pitch, lam, z, oracle.ANGULAR)
+        out[f"z_{z}"] = {arm: {k: float(f"{v:.3e}") for k, v in precision.errors(precision.run_arm(u, pitch, lam, z, arm), ref).items()}
+                         for arm in precision.ARMS}
+    return {"workload": "asm_4096_pad8192", "arms": out}
+
+
+def config_hologram(dev, steps=200):
+    """Phase-only hologram (1920 x 1080 phase in a 2048^2 canvas, padded to 4096^2, 520 nm,
+    6.4 um, z = 0.15 m): 200 Adam steps through the hand-written adjoint; seconds per step and the
+    first and last loss."""
+    from paper_1107_5578_gb300 import hologram
+    prob = hologram.HologramProblem(device=dev)
+    _, losses, dt = hologram.optimise(prob, steps=steps, lr=0.05)
+    prob.plan.close()
+    return {"workload": "hologram_1920x1080_canvas2048_pad4096", "steps": steps, "ms_per_step": round(1e3 * dt / steps, 3),
+            "loss_first": float(f"{losses[0]:.5e}"), "loss_last": float(f"{losses[-1]:.5e}")}
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -159,7 +384,8 @@ def run_reference(args, world, rank):
 
 
 def cpu_baseline_sample():
-    """Oracle throughput on this host (bounded: one 2048^2 propagation, ~seconds)."""
+    """Oracle throughput on this host (bounded: a few 2048^2 propagations, ~seconds), on all
+    threads, with one single-threaded propagation beside it."""
     import oracle
     from paper_1107_5578_gb300 import synth
     oracle.build()
@@ -173,8 +399,16 @@ def cpu_baseline_sample():
         if time.perf_counter() - t0 > 8.0 or reps >= 5:
             break
     dt = (time.perf_counter() - t0) / reps
-    return {"value": round(1.0 / dt, 4), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{reps} propagation(s) of one 2048^2 ASM field (FP64, OpenMP over rows/columns)"}
+    cores = oracle.max_threads()
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.propagate(u, PITCH, PITCH, LAM, Z, oracle.ANGULAR)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
+    return {"value": round(1.0 / dt, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} propagation(s) of one 2048^2 ASM field (FP64, OpenMP over rows/columns)",
+            "single_thread": {"value": round(1.0 / dt1, 4), "unit": UNIT, "cores": 1,
+                              "sample": "1 propagation of one 2048^2 ASM field on one thread"}}
 
 
 def stack_measurement(dev, hbm_peak):
@@ -408,7 +642,7 @@ def main():
         barrier()
         wall["t0"] = time.perf_counter()
 
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    with NvmlClockSampler(torch.cuda.current_device()) as clk:
         t_start, t_end, step_ev = timed_steps(plan, x, y, args.steps, stream, before=start)
         barrier()
         wall1 = time.perf_counter()
@@ -419,14 +653,30 @@ def main():
     ms_step = ms_total / args.steps
     value = replicas.job_rate(B * args.steps, world, ms_total / 1e3)
 
-    # per-pass averages (ms per launch) and roofline of the dominant pass
+    # per-pass averages (ms per launch); each pass against the HBM roofline (algorithmic bytes)
+    # and the FP32 arithmetic roofline (counted FP32 instructions against the measured rate)
     pp = per_pass / args.steps
     hbm_peak, sm_max, peak_kind = peaks()
+    fp32_rate = fp32_peak(dev)
     names = ["row_fwd", "col_fwd_h_inv", "row_inv"]
     dom = int(np.argmax(pp))
     pass_bytes = [24 * N * N * B, 32 * N * N * B, 24 * N * N * B]
+    passes = {}
+    for k, nm in enumerate(names):
+        gbs = pass_bytes[k] / (pp[k] / 1e3) / 1e9
+        tis = FP32_PER_PASS[nm] * B / (pp[k] / 1e3) / 1e12
+        passes[nm] = {"ms": round(pp[k], 4), "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
+                      "fp32_tinst_s": round(tis, 2), "alu_frac": round(tis / (fp32_rate / 1e12), 4)}
     achieved = pass_bytes[dom] / (pp[dom] / 1e3) / 1e9
     path_gbs = BYTES_PER_PROP * B / (sum(pp) / 1e3) / 1e9
+    hbm_roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": traffic_bytes(names[dom], B),
+                "kernel": names[dom], "peak_kind": peak_kind}
+    alu_roof = {"bound": "alu", "achieved": passes[names[dom]]["fp32_tinst_s"], "peak": round(fp32_rate / 1e12, 2),
+                "unit": "FP32 Tinst/s", "frac": passes[names[dom]]["alu_frac"], "traffic": traffic_bytes(names[dom], B),
+                "kernel": names[dom], "peak_kind": "measured (cwo_debug_ffma_rate: 16 FFMA chains per thread, best of 5)",
+                "fp32_inst_per_launch": int(FP32_PER_PASS[names[dom]] * B)}
+    roofline, roofline_other = (alu_roof, hbm_roof) if alu_roof["frac"] > hbm_roof["frac"] else (hbm_roof, alu_roof)
 
     # ---- end to end through the public API with host buffers: every step uploads its inputs
     # from pinned host memory and downloads its results; uploads, propagations and downloads of
@@ -465,6 +715,12 @@ def main():
     recalc_h = recalc_h_measurement(x, y, args.steps) if rank == 0 else None
     fresnel_b = fresnel_batch_measurement(x, y, args.steps, peaks()[0]) if rank == 0 else None
     gs_res = gs_measurement(dev) if rank == 0 else None
+    cfg_512 = config_asm_512(dev) if rank == 0 else None
+    cfg_stack = config_fresnel_stack_errors(dev) if rank == 0 else None
+    if cfg_stack is not None:
+        stack.update(cfg_stack)
+    cfg_prec = config_precision_4096(dev) if rank == 0 else None
+    cfg_holo = config_hologram(dev) if rank == 0 else None
     serve = serving_measurement(dev, args.serving_requests, args.serving_rate) \
         if args.serving_requests > 0 and rank == 0 else None
     serve_high = serving_measurement(dev, min(args.serving_requests, 20000), 4 * args.serving_rate) \
@@ -486,9 +742,10 @@ def main():
                    "l2": "inputs larger than L2 (B x 32 MiB per step), no flush",
                    "parallelism": f"independent items per rank x{world}"},
         "hbm_gbs_path": round(path_gbs, 1),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(achieved / hbm_peak, 4), "traffic": traffic_bytes(names[dom], B),
-                     "kernel": names[dom], "peak_kind": peak_kind},
+        "roofline": roofline,
+        "roofline_other": roofline_other,
+        "passes": passes,
+        "fp32_peak_tinst_s": round(fp32_rate / 1e12, 2),
         "roofline_path": {"achieved": round(path_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                           "frac": round(path_gbs / hbm_peak, 4), "bytes_per_prop": BYTES_PER_PROP},
         "passes_ms": {n: round(v, 4) for n, v in zip(names, pp)},
@@ -500,6 +757,9 @@ def main():
                 "copy_gbs": copy_gbs},
         "gpu_launches": plan.launches_per_call * args.steps,
         "fresnel_stack": stack,
+        "asm_512": cfg_512,
+        "precision_4096": cfg_prec,
+        "hologram": cfg_holo,
         "asm_recalc_h": recalc_h,
         "fresnel_batch": fresnel_b,
         "gs_kinoform": gs_res,

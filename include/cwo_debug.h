@@ -2,8 +2,9 @@
  * cwo_debug.h -- host-only diagnostic entry points of libcwo_gb300.so.
  *
  * They expose the FP64 host computations the plans are built from, so that tests can check them
- * on a machine without a GPU.  None of them touches a device, except cwo_debug_bounded_wait (the
- * last one).  They return CWO_ERR_INVALID_ARG on bad arguments (message in cwo_last_error()).
+ * on a machine without a GPU.  None of them touches a device, except cwo_debug_bounded_wait and
+ * cwo_debug_ffma_rate (the last two).  They return CWO_ERR_INVALID_ARG on bad arguments (message
+ * in cwo_last_error()).
  */
 #ifndef CWO_DEBUG_H
 #define CWO_DEBUG_H
@@ -82,6 +83,14 @@ cwo_status cwo_debug_line_fft(int p, int inverse, const float* in_ri, float* out
  * the status word stays 0.  spin_limit: polls before giving up, in [1, 2^20].  *status_out
  * receives the status word.  Returns CWO_ERR_CUDA if the launch or a copy fails. */
 cwo_status cwo_debug_bounded_wait(unsigned spin_limit, int complete, int* status_out);
+
+/* FP32 issue-rate calibration (device, asynchronous on cuda_stream): `blocks` CTAs of 256
+ * threads, each thread running `iters` (a multiple of 8) steps of 16 independent FP32 fused
+ * multiply-adds and writing one float to out_dev[blocks * 256] (device memory of the current
+ * device).  The caller times the launch: FP32 instructions = blocks * 256 * iters * 16 (2 flops
+ * each).  The paper has no counterpart; it is the measured denominator of the FFT passes'
+ * arithmetic roofline. */
+cwo_status cwo_debug_ffma_rate(int blocks, int iters, float* out_dev, void* cuda_stream);
 
 #ifdef __cplusplus
 }

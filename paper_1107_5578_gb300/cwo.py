@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
                 "cwo_debug_emulate_shifted_fresnel": ([i, i, d, d, d, d, ctypes.POINTER(ShiftedFresnel), i, vp, vp], i),
                 "cwo_debug_emulate_shifted": ([i, i, d, d, d, d, ctypes.POINTER(Shift), i, vp, vp], i),
                 "cwo_debug_bounded_wait": ([u, i, ctypes.POINTER(ctypes.c_int)], i),
+                "cwo_debug_ffma_rate": ([i, i, vp, vp], i),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)

@@ -27,11 +27,13 @@ def test_results_are_the_same_alone_and_in_the_mix(srv):
     torch, serving = srv
     sizes = (256, 512, 1024)
     pools = serving.make_pools(sizes, per_size=3)
-    mix = _requests(serving, 60, sizes)
+    # a dense stream (5 us between arrivals): requests arrive while others are on the GPU, so
+    # they travel in mixed batches
+    mix = _requests(serving, 60, sizes, rate=2e5)
     server = serving.Server(sizes=sizes, max_batch={256: 16, 512: 8, 1024: 4}, pools=pools, keep_results=True)
     server.run(mix)
     assert server.batches < len(mix)                 # batching happened
-    alone = _requests(serving, 60, sizes)
+    alone = _requests(serving, 60, sizes, rate=2e5)
     serving.serve_serial(alone, pools, keep_results=True)
     for a, b in zip(sorted(mix, key=lambda r: r.rid), sorted(alone, key=lambda r: r.rid)):
         assert torch.equal(a.result, b.result), a.rid

@@ -251,3 +251,8 @@ def test_host_emulation_of_shifted_asm_matches_the_oracle(lib, n, dx, lam, z, sh
     got = cwo.emulate_shifted(u, dx, dx, lam, z, sh, adjoint=bool(adjoint))
     want = oracle.propagate_shifted(u, dx, dx, lam, z, *shift, flags=oracle.ADJOINT if adjoint else 0)
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-5
+
+
+def test_ffma_calibration_rejects_bad_arguments_on_the_host(lib):
+    for blocks, iters in ((0, 8), (4, 7), (4, 0), (1 << 21, 8)):
+        assert lib.cwo_debug_ffma_rate(blocks, iters, None, None) == cwo.ERR_INVALID_ARG
