@@ -99,9 +99,116 @@ k_line_conv(const float2* __restrict__ in, long long in_item_stride, const __gri
 template <int P>
 __host__ __device__ constexpr int line_stage_stride() { return P / 2 + 4; }
 
+// exchange / tile region of the persistent form: the pair layout of the 128-bit exchanges
+// (P >= 128) or the padded layout, and the dense [position][line] tile, which aliases it
+// (the largest of the three, so that one staging offset serves every persistent line kernel)
+template <int P, int R>
+__host__ __device__ constexpr size_t line_p_xwords() {
+    return 2 * (size_t)PairLayout<P, (R / 2 > 0 ? R / 2 : 1)>::SLOTS > line_smem_words<P, R>()
+               ? 2 * (size_t)PairLayout<P, (R / 2 > 0 ? R / 2 : 1)>::SLOTS
+               : line_smem_words<P, R>();
+}
+
 template <int P, int R>
 __host__ __device__ constexpr size_t line_p_smem_bytes() {
-    return (line_smem_words<P, R>() + (size_t)R * line_stage_stride<P>()) * sizeof(float2) + sizeof(uint64_t);
+    return (line_p_xwords<P, R>() + (size_t)R * line_stage_stride<P>()) * sizeof(float2) + sizeof(uint64_t);
+}
+
+struct LineGroupArgs {
+    const float2* in;
+    long long in_item_stride;
+    const CUtensorMap* omap;
+    const float2* h;
+    long long h_item_stride;
+    const float4* tw;
+    const float2* pre;
+    const float2* post;
+    float2* stage;
+    uint64_t* mbar;
+    int conj;
+    float scale;
+    int groups_per_item;
+};
+
+// thread 0: the R lines of group g into the staging buffer (completion on the mbarrier)
+template <int P, int R>
+__device__ __forceinline__ void line_issue(const LineGroupArgs& A, int g) {
+    constexpr int N = P / 2, SST = line_stage_stride<P>();
+    const int item = g / A.groups_per_item, l0 = (g % A.groups_per_item) * R;
+    const float2* src = A.in + item * A.in_item_stride + (long long)l0 * N;
+    mbar_arrive_expect_tx(A.mbar, (unsigned)(R * N * sizeof(float2)));
+#pragma unroll 1
+    for (int rr = 0; rr < R; ++rr) bulk_load(A.stage + rr * SST, src + rr * N, (unsigned)(N * sizeof(float2)), A.mbar);
+}
+
+// One group of R lines (P >= 512): read the staged lines, request the next group's, transform,
+// multiply by the axis table, transform back, write the kept half into the tile and store it by
+// TMA.  Returns false (every thread) when the staged copy did not land.  A separate function
+// keeps the loop's state out of the registers the transform needs.
+template <int P, int R, bool FAC>
+__device__ __noinline__ bool line_group(const LineGroupArgs& A, int g, int gnext, bool ok) {
+    constexpr int T = P / 16, N = P / 2, SST = line_stage_stride<P>(), CP = R / 2;
+    constexpr int BOX = N < kTmaBoxCols ? N : kTmaBoxCols;
+    extern __shared__ __align__(1024) float2 sm[];
+    float4* sx = reinterpret_cast<float4*>(sm);
+    const int t = threadIdx.x % T, cp = threadIdx.x / T, c0 = 2 * cp;
+    float2 a[16], b[16];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {   // stage-0 positions t + e P/16 of lines c0 and c0 + 1
+        a[e] = A.stage[c0 * SST + t + e * T];
+        b[e] = A.stage[(c0 + 1) * SST + t + e * T];
+    }
+#pragma unroll
+    for (int e = 8; e < 16; ++e) { a[e] = make_float2(0.f, 0.f); b[e] = make_float2(0.f, 0.f); }
+    if constexpr (FAC) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float2 f = __ldg(A.pre + t + e * T);
+            a[e] = cmul(a[e], f);
+            b[e] = cmul(b[e], f);
+        }
+    }
+    fence_proxy_async_smem();   // these reads of the staging buffer precede the next bulk copy into it
+    if (__syncthreads_or(!ok)) return false;                              // a copy did not land
+    if (threadIdx.x == 0 && gnext >= 0) line_issue<P, R>(A, gnext);
+    stage_butterflies<P, 0, false, 8>(a);
+    stage_butterflies<P, 0, false, 8>(b);
+    twiddle2<P, 0, false>(a, b, A.tw, t);
+    if (threadIdx.x == 0) tma_store_wait_read();                          // previous tile read out
+    __syncthreads();
+    xch2v<P, CP, 0, 1>(sx, cp, t, a, b);
+    fwd2v_from<P, CP, 1, 8>(a, b, sx, cp, t, A.tw);
+    {
+        const float2* hh = A.h + (g / A.groups_per_item) * A.h_item_stride + t;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const float2 w = __ldg(hh + e * T);
+            a[e] = A.conj ? cmulc(a[e], w) : cmul(a[e], w);
+            b[e] = A.conj ? cmulc(b[e], w) : cmul(b[e], w);
+        }
+    }
+    inv2v_from<P, CP, Geo<P>::NST - 1>(a, b, sx, cp, t, A.tw);
+    __syncthreads();   // every exchange read done before the tile (which aliases the region) is written
+    // kept positions t + e T (e < 8) of lines c0, c0 + 1: tile words (t + e T) R + c0, + 1
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        float2 x = cscale(a[e], A.scale), y = cscale(b[e], A.scale);
+        if constexpr (FAC) {
+            const float2 q = __ldg(A.post + t + e * T);
+            x = cmul(x, q);
+            y = cmul(y, q);
+        }
+        *reinterpret_cast<float4*>(sm + (t + e * T) * R + c0) = make_float4(x.x, x.y, y.x, y.y);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int item = g / A.groups_per_item, l0 = (g % A.groups_per_item) * R;
+#pragma unroll 1
+        for (int bx = 0; bx < N / BOX; ++bx) tma_store_3d(A.omap, sm + bx * BOX * R, l0, bx * BOX, item);
+        tma_store_commit();
+    }
+    return true;
 }
 
 template <int P, int R, bool FAC>
@@ -110,87 +217,26 @@ k_line_conv_p(const float2* __restrict__ in, long long in_item_stride, const __g
               const float2* __restrict__ h, long long h_item_stride, int conj, float scale,
               const float4* __restrict__ tw, int groups_per_item, int total_groups, int* status,
               const float2* __restrict__ pre, const float2* __restrict__ post) {
+    static_assert(P >= 512, "the persistent line pass needs T >= 32");
     pdl_wait();
-    constexpr int T = P / 16, N = P / 2, SST = line_stage_stride<P>();
-    constexpr int BOX = N < kTmaBoxCols ? N : kTmaBoxCols;
-    using Lay = PadLayout<P, R>;
+    constexpr int SST = line_stage_stride<P>();
     extern __shared__ __align__(1024) float2 sm[];
-    float2* stage = sm + line_smem_words<P, R>();
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(stage + R * SST);
-    const int t = threadIdx.x % T, c0 = 2 * (threadIdx.x / T);
-    auto issue = [&](int g) {   // thread 0: the R lines of group g into the staging buffer
-        const int item = g / groups_per_item, l0 = (g % groups_per_item) * R;
-        const float2* src = in + item * in_item_stride + (long long)l0 * N;
-        mbar_arrive_expect_tx(mbar, (unsigned)(R * N * sizeof(float2)));
-#pragma unroll 1
-        for (int rr = 0; rr < R; ++rr) bulk_load(stage + rr * SST, src + rr * N, (unsigned)(N * sizeof(float2)), mbar);
-    };
+    LineGroupArgs A;
+    A.in = in; A.in_item_stride = in_item_stride; A.omap = &omap; A.h = h; A.h_item_stride = h_item_stride;
+    A.tw = tw; A.pre = pre; A.post = post; A.conj = conj; A.scale = scale; A.groups_per_item = groups_per_item;
+    A.stage = sm + line_p_xwords<P, R>();
+    A.mbar = reinterpret_cast<uint64_t*>(A.stage + R * SST);
     if (threadIdx.x == 0) {
-        mbar_init(mbar, 1);
-        if ((int)blockIdx.x < total_groups) issue(blockIdx.x);
+        mbar_init(A.mbar, 1);
+        if ((int)blockIdx.x < total_groups) line_issue<P, R>(A, blockIdx.x);
     }
     __syncthreads();
     unsigned parity = 0;
 #pragma unroll 1
     for (int g = blockIdx.x; g < total_groups; g += gridDim.x, parity ^= 1u) {
-        const bool ok = mbar_wait_bounded(mbar, parity, status);
-        float2 a[16], b[16];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {   // stage-0 positions t + e P/16 of lines c0 and c0 + 1
-            a[e] = stage[c0 * SST + t + e * T];
-            b[e] = stage[(c0 + 1) * SST + t + e * T];
-        }
-#pragma unroll
-        for (int e = 8; e < 16; ++e) { a[e] = make_float2(0.f, 0.f); b[e] = make_float2(0.f, 0.f); }
-        if constexpr (FAC) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const float2 f = __ldg(pre + t + e * T);
-                a[e] = cmul(a[e], f);
-                b[e] = cmul(b[e], f);
-            }
-        }
-        fence_proxy_async_smem();   // these reads of the staging buffer precede the next bulk copy into it
-        if (__syncthreads_or(!ok)) break;                                // a copy did not land
-        if (threadIdx.x == 0 && g + (int)gridDim.x < total_groups) issue(g + gridDim.x);
-        stage_butterflies<P, 0, false, 8>(a);
-        stage_butterflies<P, 0, false, 8>(b);
-        if constexpr (Geo<P>::NST > 1) twiddle2<P, 0, false>(a, b, tw, t);
-        if (threadIdx.x == 0) tma_store_wait_read();                      // previous tile read out
-        __syncthreads();
-        if constexpr (Geo<P>::NST > 1) {
-            exchange2<P, R, Lay, 0, 1, 0, 0>(sm, c0, t, a, b);
-            fwd2_from<P, R, Lay, 1, 8, 0>(a, b, sm, c0, t, tw);
-        }
-        {
-            const float2* hh = h + (g / groups_per_item) * h_item_stride + t;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const float2 w = __ldg(hh + e * T);
-                a[e] = conj ? cmulc(a[e], w) : cmul(a[e], w);
-                b[e] = conj ? cmulc(b[e], w) : cmul(b[e], w);
-            }
-        }
-        inv2_from<P, R, Lay, Geo<P>::NST - 1, 0, 0>(a, b, sm, c0, t, tw);
-        // kept positions t + e T (e < 8) of lines c0, c0 + 1: tile words (t + e T) R + c0, + 1
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            float2 x = cscale(a[e], scale), y = cscale(b[e], scale);
-            if constexpr (FAC) {
-                const float2 q = __ldg(post + t + e * T);
-                x = cmul(x, q);
-                y = cmul(y, q);
-            }
-            *reinterpret_cast<float4*>(sm + (t + e * T) * R + c0) = make_float4(x.x, x.y, y.x, y.y);
-        }
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int item = g / groups_per_item, l0 = (g % groups_per_item) * R;
-#pragma unroll 1
-            for (int bx = 0; bx < N / BOX; ++bx) tma_store_3d(&omap, sm + bx * BOX * R, l0, bx * BOX, item);
-            tma_store_commit();
-        }
+        const bool ok = mbar_wait_bounded(A.mbar, parity, status);
+        const int gnext = g + (int)gridDim.x < total_groups ? g + (int)gridDim.x : -1;
+        if (!line_group<P, R, FAC>(A, g, gnext, ok)) break;
     }
     if (threadIdx.x == 0) tma_store_wait_read();
 }
@@ -210,7 +256,7 @@ k_line_stack_p(const float2* __restrict__ in, const __grid_constant__ CUtensorMa
     constexpr int BOX = N < kTmaBoxCols ? N : kTmaBoxCols;
     using Lay = PadLayout<P, R>;
     extern __shared__ __align__(1024) float2 sm[];
-    float2* stage = sm + line_smem_words<P, R>();
+    float2* stage = sm + line_p_xwords<P, R>();
     uint64_t* mbar = reinterpret_cast<uint64_t*>(stage + R * SST);
     const int r = threadIdx.x % R, t = threadIdx.x / R;
     auto issue = [&](int g) {   // thread 0: the R source lines of group g into the staging buffer
@@ -304,7 +350,8 @@ static cudaError_t line_conv_impl(const float2* in, long long in_item_stride, co
     constexpr int T = P / 16;
     if (lines % R || items < 1 || items > 65535) return cudaErrorInvalidValue;
     const bool aligned = ((uintptr_t)in % 16 == 0) && (in_item_stride % 2 == 0);
-    if (P >= 512 && aligned && status) {
+    if constexpr (P >= 512) {
+    if (aligned && status) {
         const size_t smem = line_p_smem_bytes<P, R>();
         int resident = 0;
         cudaError_t e = kernel_setup<k_line_conv_p<P, R, FAC>>(smem, (R / 2) * T, &resident);
@@ -314,6 +361,7 @@ static cudaError_t line_conv_impl(const float2* in, long long in_item_stride, co
         if (grid > 0)
             return pdl_launch(k_line_conv_p<P, R, FAC>, dim3(grid), dim3((R / 2) * T), smem, st, in, in_item_stride,
                               *omap, h, h_item_stride, conj, scale, tw, lines / R, groups, status, pre, post);
+    }
     }
     const size_t smem = line_smem_words<P, R>() * sizeof(float2);
     cudaError_t e = kernel_setup<k_line_conv<P, R, FAC>>(smem, R * T, nullptr);
