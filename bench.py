@@ -37,9 +37,10 @@ COL_BYTES_PER_PROP = 32 * N * N      # column pass: read + write the Ny x Px int
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each pass at batch 16,
-# from one ncu capture of the current kernels; scaled by the batch (traffic grows in proportion to
-# the fields processed).  Empty until the current kernels have been captured.
-NCU_TRAFFIC_B16 = {}
+# from one ncu capture of the current kernels (profiles/asm_2048_batch16_launches.md); scaled by
+# the batch (traffic grows in proportion to the fields processed).  The column pass reads the
+# 67 MB transfer-function table of the plan once per launch besides its 16 fields.
+NCU_TRAFFIC_B16 = {"row_fwd": 1555.59e6, "col_fwd_h_inv": 2151.98e6, "row_inv": 1600.07e6}
 
 
 def traffic_bytes(kernel, batch):
@@ -591,11 +592,16 @@ def main():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="the headline workload only (no e2e, secondary workloads, serving or CPU baseline): "
+                         "for profiler launch lists")
     ap.add_argument("--serving-requests", type=int, default=100000,
                     help="requests of the mixed-size serving stream (0 skips the serving measurements)")
     ap.add_argument("--serving-rate", type=float, default=2000.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.headline_only:
+        args.serving_requests, args.no_cpu_baseline = 0, True
     if args.steps is None:
         args.steps = 20 if args.impl == "reference" else 500
     world, rank, local = dist_setup()
@@ -711,16 +717,17 @@ def main():
     copy_gbs = {"h2d": round(host_in.numel() * 8 / (c0.elapsed_time(c1) / 1e3) / 1e9, 1),
                 "d2h": round(host_out.numel() * 8 / (c1.elapsed_time(c2) / 1e3) / 1e9, 1)}
 
-    stack = stack_measurement(dev, peaks()[0])
-    recalc_h = recalc_h_measurement(x, y, args.steps) if rank == 0 else None
-    fresnel_b = fresnel_batch_measurement(x, y, args.steps, peaks()[0]) if rank == 0 else None
-    gs_res = gs_measurement(dev) if rank == 0 else None
-    cfg_512 = config_asm_512(dev) if rank == 0 else None
-    cfg_stack = config_fresnel_stack_errors(dev) if rank == 0 else None
+    extra = rank == 0 and not args.headline_only        # the secondary workloads and configs
+    stack = stack_measurement(dev, peaks()[0]) if extra else None
+    recalc_h = recalc_h_measurement(x, y, args.steps) if extra else None
+    fresnel_b = fresnel_batch_measurement(x, y, args.steps, peaks()[0]) if extra else None
+    gs_res = gs_measurement(dev) if extra else None
+    cfg_512 = config_asm_512(dev) if extra else None
+    cfg_stack = config_fresnel_stack_errors(dev) if extra else None
     if cfg_stack is not None:
         stack.update(cfg_stack)
-    cfg_prec = config_precision_4096(dev) if rank == 0 else None
-    cfg_holo = config_hologram(dev) if rank == 0 else None
+    cfg_prec = config_precision_4096(dev) if extra else None
+    cfg_holo = config_hologram(dev) if extra else None
     serve = serving_measurement(dev, args.serving_requests, args.serving_rate) \
         if args.serving_requests > 0 and rank == 0 else None
     serve_high = serving_measurement(dev, min(args.serving_requests, 20000), 4 * args.serving_rate) \
