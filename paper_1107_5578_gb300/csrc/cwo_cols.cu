@@ -27,98 +27,6 @@
 
 namespace cwo {
 
-__device__ __forceinline__ float2 asm_h_fp32(int kbx, int kby, const HParams& hp) {
-    // Eq. ang2 evaluated literally in single precision (precision-study arm)
-    const float fx = (float)kbx * (float)hp.dfx, fy = (float)kby * (float)hp.dfy;
-    const float k = (float)hp.k;
-    const float fourpi2 = 39.4784176043574344753f;
-    const float rad = k * k - fourpi2 * (fx * fx + fy * fy);
-    if (rad < 0.0f) return make_float2(0.f, 0.f);
-    const float ph = (float)hp.z * sqrtf(rad);
-    float sn, cs;
-    sincosf(ph, &sn, &cs);
-    return make_float2(cs, sn);
-}
-
-// Evaluate the transfer function of storage column `col` at this thread's 16 axis indices
-// e * T + t (DIF order) and hand each value to f(e, h).  The mode and tables are the launch's, or
-// the item's own in a mixed batch.
-template <int P, bool MIXED, class F>
-__device__ __forceinline__ void eval_h(int col, int t, long long item, const HParams& hp, F&& f) {
-    constexpr int T = P / 16;
-    int mode = hp.mode;
-    float K = 0.f;
-    double Kd = hp.K, sx = hp.sx, sy = hp.sy;
-    if (MIXED) {      // mixed batch: this item's own mode and scalars (uniform across the block)
-        const ItemParams ip = hp.items[item];
-        mode = ip.mode;
-        K = ip.kf;
-        Kd = ip.K; sx = ip.sx; sy = ip.sy;
-    } else if (mode == HMODE_ASM_POLY || mode == HMODE_ASM_EXACT) {
-        K = __ldg(hp.kf + item * hp.kf_item_stride);
-    }
-    if (mode == HMODE_TABLE) {
-        const int j = abs(__ldg(hp.kbx + col));
-        const float2* hc = hp.hcache + (long long)j * hp.hcache_stride + t;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) f(e, __ldg(hc + e * T));
-    } else if (mode == HMODE_FRESNEL) {
-        if (MIXED) {
-            const float4 X = __ldg(hp.ax + item * hp.x_item_stride + col);
-            const float2 hxc = make_float2(X.x, X.y);
-            const float4* hy = hp.ay + item * hp.y_item_stride + t;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const float4 Y = __ldg(hy + e * T);
-                f(e, cmul(hxc, make_float2(Y.x, Y.y)));
-            }
-        } else {
-            const float2 hxc = __ldg(hp.hx + item * hp.x_item_stride + col);
-            const float2* hy = hp.hy + item * hp.y_item_stride + t;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) f(e, cmul(hxc, __ldg(hy + e * T)));
-        }
-    } else if (mode == HMODE_ASM_POLY || mode == HMODE_ASM_EXACT) {
-        const float4 X = __ldg(hp.ax + item * hp.x_item_stride + col);
-        const float4* ay = hp.ay + item * hp.y_item_stride + t;
-        if (mode == HMODE_ASM_POLY) {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) f(e, asm_h_reduced<true>(X, __ldg(ay + e * T), K));
-        } else {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) f(e, asm_h_reduced<false>(X, __ldg(ay + e * T), K));
-        }
-    } else {
-        const int kbx = __ldg(hp.kbx + col);
-        if (hp.asym) {   // shifted ASM, per-element FP64: window and shift phase
-            const bool inx = kbx >= hp.wxlo && kbx <= hp.wxhi;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int kby = __ldg(hp.kby + e * T + t);
-                const bool in = inx && kby >= hp.wylo && kby <= hp.wyhi;
-                f(e, in ? asm_h_fp64_shifted(kbx, kby, Kd, sx, sy, hp.shx, hp.shy) : make_float2(0.f, 0.f));
-            }
-            return;
-        }
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int kby = __ldg(hp.kby + e * T + t);
-            f(e, mode == HMODE_ASM_FP32 ? asm_h_fp32(kbx, kby, hp) : asm_h_fp64(kbx, kby, Kd, sx, sy));
-        }
-    }
-}
-
-// multiply the registers of NV transforms of the same storage column pair (same |kx|) by H
-// (by conj(H) for the adjoint)
-template <int P, int NV, bool MIXED = false>
-__device__ __forceinline__ void apply_h(float2 (&a)[16], float2 (&b)[16], int col, int t, long long item,
-                                        const HParams& hp) {
-    eval_h<P, MIXED>(col, t, item, hp, [&](int e, float2 h) {
-        a[e] = hp.conj ? cmulc(a[e], h) : cmul(a[e], h);
-        if (NV == 2) b[e] = hp.conj ? cmulc(b[e], h) : cmul(b[e], h);
-    });
-}
-
 // columns per block (single-column kernel) and mirror pairs per block (paired kernel)
 template <int P> constexpr int cols_per_block() {
     constexpr int T = P / 16;

@@ -495,6 +495,18 @@ __device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ s
     }
 }
 
+// Adjoint stages from stage S down to (and including the exchange into) stage 0; the caller
+// applies the stage-0 twiddles and butterflies (the inverse row pass overlaps the next tile's
+// load with them).
+template <int P, int C, class Lay, int S, int PING, int XOFF, class Tw>
+__device__ __forceinline__ void inv_to_stage0(float2 (&v)[16], float2* __restrict__ sm, int c, int t, const Tw& tw) {
+    using G = Geo<P>;
+    if constexpr (S < G::NST - 1) tw.template apply<S, true>(v);
+    stage_butterflies<P, S, true, 16>(v);
+    exchange<P, C, Lay, S, S - 1, PING, XOFF + (G::NST - 1 - S)>(sm, c, t, v);
+    if constexpr (S > 1) inv_to_stage0<P, C, Lay, S - 1, PING, XOFF>(v, sm, c, t, tw);
+}
+
 #endif  // __CUDACC__
 
 }  // namespace cwo

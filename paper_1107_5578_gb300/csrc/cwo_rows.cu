@@ -23,6 +23,7 @@
 #include "cwo_internal.h"
 #include "cwo_launch.cuh"
 #include "cwo_tma.cuh"
+#include "cwo_epilogue.cuh"
 
 namespace cwo {
 
@@ -80,30 +81,6 @@ k_row_fwd(const float2* __restrict__ in, long long in_item_stride, const __grid_
         for (int b = 0; b < P / BOX; ++b) tma_store_3d(&wmap, sm + b * BOX * R, y0, b * BOX, item + item_off);
         tma_store_commit_and_drain();
     }
-}
-
-// Output epilogue of the inverse row pass, applied to the scaled value w of output element idx
-// (the GS constraints of Section "GS algorithm" fused into the pass that produces the field):
-//   EPI_NONE       out = w
-//   EPI_PHASE      out = w / |w|             (phase constraint; |w| = 0 gives 1)
-//   EPI_AMPLITUDE  out = amp[idx] w / |w|    (amplitude constraint)
-//   EPI_INTENSITY  inten[idx] = |w|^2        (reconstruction; out is not written)
-__device__ __forceinline__ float2 unit_phase(float2 w) {
-    const float m2 = w.x * w.x + w.y * w.y;
-    if (m2 > 0.f) {
-        const float r = rsqrtf(m2);
-        return make_float2(w.x * r, w.y * r);
-    }
-    return make_float2(1.f, 0.f);
-}
-
-template <int EPI>
-__device__ __forceinline__ void epilogue_store(float2* out, const Epilogue& ep, long long idx, int x, int y, float2 w) {
-    if constexpr (EPI == EPI_NONE) out[idx] = w;
-    else if constexpr (EPI == EPI_SEPARABLE) out[idx] = cmul(w, cmul(__ldg(ep.qx + x), __ldg(ep.qy + y)));
-    else if constexpr (EPI == EPI_PHASE) out[idx] = unit_phase(w);
-    else if constexpr (EPI == EPI_AMPLITUDE) out[idx] = cscale(unit_phase(w), __ldg(ep.amp + idx));
-    else ep.inten[idx] = w.x * w.x + w.y * w.y;
 }
 
 template <int P, int R, int EPI>
@@ -323,15 +300,6 @@ k_row_fwd_c(const float2* __restrict__ in, long long in_item_stride, const __gri
 // Inverse, persistent: R rows per group, one tile buffer.  The tile of the NEXT group is
 // requested as soon as the last exchange of the current group has been read back, so its load
 // overlaps the last stage, the crop and the stores of the current group.
-template <int P, int C, class Lay, int S, int PING, int XOFF, class Tw>
-__device__ __forceinline__ void inv_to_stage0(float2 (&v)[16], float2* __restrict__ sm, int c, int t, const Tw& tw) {
-    using G = Geo<P>;
-    if constexpr (S < G::NST - 1) tw.template apply<S, true>(v);
-    stage_butterflies<P, S, true, 16>(v);
-    exchange<P, C, Lay, S, S - 1, PING, XOFF + (G::NST - 1 - S)>(sm, c, t, v);
-    if constexpr (S > 1) inv_to_stage0<P, C, Lay, S - 1, PING, XOFF>(v, sm, c, t, tw);
-}
-
 template <int P, int R> constexpr int row_inv_p_min_blocks() { return R * (P / 16) >= 1024 ? 1 : 1024 / (R * (P / 16)); }
 
 template <int P, int R, int EPI>
