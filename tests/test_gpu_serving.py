@@ -73,3 +73,17 @@ def test_submit_field_returns_a_future(srv):
     small = serving.Server(sizes=(128,), max_batch={128: 4}, mem_budget=1000)
     with pytest.raises(ValueError):                                # one field exceeds the budget
         small.submit_field(torch.zeros(128, 128, dtype=torch.complex64, device="cuda"), z=0.1)
+
+
+def test_server_refuses_a_host_field_before_queueing_it(srv):
+    torch, serving = srv
+    server = serving.Server(sizes=(128,), max_batch={128: 4}, keep_results=True)
+    host = torch.zeros(128, 128, dtype=torch.complex64)             # host memory
+    req = serving.Request(1, 128, 0, 0.05, 532e-9, 8e-6, field=host)
+    with pytest.raises(ValueError):
+        server.submit(req)
+    assert server.pending() == 0
+    ok = server.submit_field(torch.ones(128, 128, dtype=torch.complex64, device="cuda"), z=0.05,
+                             wavelength=532e-9, pitch=8e-6)
+    assert server.wait(ok) is not None                               # the server still serves
+    server.close()

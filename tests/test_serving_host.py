@@ -59,3 +59,39 @@ def test_admission_by_memory_budget():
             while c > 0 and used + per[c] > big:
                 c //= 2
             assert b == c
+
+
+def test_native_server_refuses_bad_arguments_before_touching_a_device():
+    """The runtime's argument checks run on the host first (no GPU is needed to see them)."""
+    pytest.importorskip("torch")
+    import ctypes
+    from paper_1107_5578_gb300 import build, cwo, serving
+    build.build()
+    L = serving._lib()
+    out = ctypes.c_void_p()
+
+    def create(sizes, caps, slots=2, budget=0):
+        s = (ctypes.c_int * len(sizes))(*sizes)
+        c = (ctypes.c_int * len(caps))(*caps)
+        return L.cwo_server_create(len(sizes), s, c, slots, budget, ctypes.byref(out))
+
+    assert create([], []) == cwo.ERR_INVALID_ARG                         # no size
+    assert create([300], [4]) == cwo.ERR_INVALID_ARG                     # not a power of two
+    assert create([8192], [1]) == cwo.ERR_INVALID_ARG                    # above 4096
+    assert create([256], [65]) == cwo.ERR_INVALID_ARG                    # batch capacity above 64
+    assert create([256], [0]) == cwo.ERR_INVALID_ARG
+    assert create([256, 256], [4, 4]) == cwo.ERR_INVALID_ARG             # size given twice
+    assert create([256], [4], slots=0) == cwo.ERR_INVALID_ARG
+    assert create([256], [4], slots=9) == cwo.ERR_INVALID_ARG
+    assert L.cwo_server_create(1, None, None, 2, 0, ctypes.byref(out)) == cwo.ERR_INVALID_ARG
+    b = ctypes.c_size_t(0)
+    assert L.cwo_server_batch_bytes(100, 1, ctypes.byref(b)) == cwo.ERR_INVALID_ARG
+    assert L.cwo_server_batch_bytes(256, 0, ctypes.byref(b)) == cwo.ERR_INVALID_ARG
+    take = ctypes.c_int(0)
+    assert L.cwo_server_admit(-1, 4, 0, 1 << 30, 256, ctypes.byref(take)) == cwo.ERR_INVALID_ARG
+    assert L.cwo_server_admit(4, 0, 0, 1 << 30, 256, ctypes.byref(take)) == cwo.ERR_INVALID_ARG
+    assert L.cwo_server_admit(4, 4, 0, 1 << 30, 256, None) == cwo.ERR_INVALID_ARG
+    assert L.cwo_server_submit(None, None, None) == cwo.ERR_INVALID_ARG
+    assert L.cwo_server_step(None, None) == cwo.ERR_INVALID_ARG
+    assert L.cwo_server_done(None, 0, None) == -1
+    assert L.cwo_server_destroy(None) == cwo.OK
