@@ -1,0 +1,252 @@
+// cwo_cols.cuh -- the column pass: forward FFT down each column, transfer-function multiply,
+// inverse FFT, crop to the Ny source rows -- the "FFT", "multiply by H" and "IFFT" steps of
+// Eqs. ang3 / fre_conv_fft along y, fused in one kernel.
+//
+// The intermediate is column-major ([items][Px][Ny]), so each column is Ny contiguous complex64
+// values and every global access of this pass is a coalesced 256-byte warp transaction.  Rows
+// Ny .. Py-1 are the zero padding, seen as constant zeros by the first DIF stage.  The forward transform ends in DIF (digit-reversed) order, the
+// transfer function is generated for that order, and the inverse (the exact adjoint of the
+// forward stages) starts from it: no reordering and no exchange between the last forward and the
+// first inverse stage.  Only the Ny kept rows are written back.
+//
+// Transfer functions:
+//   ASM (Eq. ang2), phase in cycles  psi = K sqrt(1 - s),  K = z / lambda,  s = a_x + a_y,
+//   a = lambda^2 f^2.  Split exactly as
+//       K sqrt(1-s) = K - [K a_x/2 + K a_x^2/8] - [K a_y/2 + K a_y^2/8] - K a_x a_y / 4 - tail,
+//       tail = K s^3 (3 + q) / (8 (1 + q)^3),  q = sqrt(1 - s),
+//   the bracketed per-axis terms (up to ~1e4 cycles) and frac(K) are range-reduced in FP64 on
+//   the host; the cross term (up to ~12 cycles) is a float-float product of two per-axis values
+//   reduced exactly in FP32; the tail is < 1 cycle.  s > 1 (evanescent) gives H = 0.
+//   Fresnel (Eq. fre_conv_fft): H = C * Hx[kx] * Hy[ky], the two 1-D DFTs of the sampled
+//   impulse response computed in FP64 per plan (h_F is separable).
+#pragma once
+#include "cwo_fft.cuh"
+#include "cwo_internal.h"
+#include "cwo_h.cuh"
+#include "cwo_launch.cuh"
+
+
+namespace cwo {
+
+// columns per block (single-column kernel) and mirror pairs per block (paired kernel)
+template <int P> constexpr int cols_per_block() {
+    constexpr int T = P / 16;
+    constexpr int c = 256 / T;
+    return c < 1 ? 1 : (c > 16 ? 16 : c);
+}
+template <int P> constexpr int col_min_blocks() { return (P / 16) * cols_per_block<P>() <= 256 ? 2 : 1; }
+// the paired kernel holds 32 values per thread (128 registers): two 256-thread CTAs per SM up to
+// P = 4096, one 512-thread CTA at P = 8192 (measured 382 us per 4096^2 field vs 488 for the
+// single-column kernel)
+template <int P> constexpr bool col_paired() { return true; }
+// single column per transform (used where the paired kernel would not fit in registers)
+template <int P, int C, bool MIXED>
+__global__ void __launch_bounds__(C * (P / 16), col_min_blocks<P>())
+k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
+      long long wout_item_stride, const float4* __restrict__ tw, const HParams hp) {
+    pdl_wait();
+    constexpr int T = P / 16, NY = P / 2;
+    using Lay = PadLayout<P, C>;
+    extern __shared__ float2 sm[];
+    const int t = threadIdx.x % T, c = threadIdx.x / T;
+    const int col = blockIdx.x * C + c;
+    const long long item = blockIdx.y;
+    const float2* src = win + item * win_item_stride + (long long)col * NY;
+    float2 v[16];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = src[t + e * T];           // rows t + e P/16 < Ny
+#pragma unroll
+    for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);   // zero padding rows
+    const TwTable<P> twt{tw, t};
+    fwd_from<P, C, Lay, 0, 8, 0>(v, sm, c, t, twt);
+    apply_h<P, 1, MIXED>(v, v, col, t, item, hp);
+    inv_from<P, C, Lay, Geo<P>::NST - 1, 0, 0>(v, sm, c, t, twt);
+    float2* dst = wout + item * wout_item_stride + (long long)col * NY;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) dst[t + e * T] = v[e];           // crop: rows < Ny
+}
+
+// Mirror-pair column kernel: a thread transforms the two storage columns of frequencies +kx and
+// -kx.  H depends on kx only through kx^2 (both methods), so the transfer function is evaluated
+// (or loaded) once for both, and the twiddles of each stage are loaded once for both.  The
+// exchanges take one barrier each (warp-wide after the first stage) and move a pair's two values
+// at one position with one 128-bit access (P >= 128; P = 8192 keeps 64-bit accesses, which fit in
+// the registers without spilling).  The grid is (items, pair groups), item fastest, so that the
+// CTAs running at one time share few pair groups: the transfer-function values of a pair (the
+// cached table of a once-calculation plan) are read from HBM once and from L2 by the other items.
+// Thread 0 prefetches into L2 the columns of the CTA that will take this CTA's place (`resident`
+// CTAs later in launch order).
+template <int P, int CP>
+constexpr int colp_smem_words() {
+    return (P >= 128 && P < 8192) ? 2 * PairLayout<P, CP>::SLOTS : PadLayout<P, 2 * CP>::WORDS;
+}
+
+template <int P, int CP, bool MIXED>
+__global__ void __launch_bounds__(CP * (P / 16), CP * (P / 16) >= 512 ? 1 : 2)
+k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
+       long long wout_item_stride, const float4* __restrict__ tw, const HParams hp, int resident) {
+    pdl_wait();
+    constexpr int T = P / 16, NY = P / 2;
+    extern __shared__ float2 sm[];
+    const int t = CP == 1 ? (int)threadIdx.x : (int)threadIdx.x % T;
+    const int cp = CP == 1 ? 0 : (int)threadIdx.x / T;
+    if (threadIdx.x == 0) {
+        const long long nb = (long long)blockIdx.y * gridDim.x + blockIdx.x + resident;
+        if (nb < (long long)gridDim.x * gridDim.y) {
+            const long long itn = nb % gridDim.x;
+            const int gn = (int)(nb / gridDim.x);
+            for (int c = 0; c < CP; ++c) {
+                const int jn = gn * CP + c;
+                if (jn >= hp.npairs) break;
+                const int2 pn = __ldg(hp.pairs + jn);
+                const float2* p0 = win + itn * win_item_stride + (long long)pn.x * NY;
+                const float2* p1 = win + itn * win_item_stride + (long long)pn.y * NY;
+                if ((((uintptr_t)p0 | (uintptr_t)p1) & 15) == 0) {
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p0), "r"(NY * 8) : "memory");
+                    if (pn.y != pn.x)
+                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p1), "r"(NY * 8) : "memory");
+                }
+            }
+        }
+    }
+    const int j = blockIdx.y * CP + cp;
+    const bool live = j < hp.npairs;
+    const int2 pr = __ldg(hp.pairs + (live ? j : 0));
+    const long long item = blockIdx.x;
+    const float2* sa = win + item * win_item_stride + (long long)pr.x * NY;
+    const float2* sb = win + item * win_item_stride + (long long)pr.y * NY;
+    float2 a[16], b[16];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) { a[e] = sa[t + e * T]; b[e] = sb[t + e * T]; }
+#pragma unroll
+    for (int e = 8; e < 16; ++e) { a[e] = make_float2(0.f, 0.f); b[e] = make_float2(0.f, 0.f); }
+    if constexpr (P >= 128 && P < 8192) {
+        fwd2v_from<P, CP, 0, 8>(a, b, reinterpret_cast<float4*>(sm), cp, t, tw);
+        apply_h<P, 2, MIXED>(a, b, pr.x, t, item, hp);
+        inv2v_from<P, CP, Geo<P>::NST - 1>(a, b, reinterpret_cast<float4*>(sm), cp, t, tw);
+    } else {
+        using Lay = PadLayout<P, 2 * CP>;
+        fwd2x_from<P, CP, Lay, 0, 8>(a, b, sm, cp, t, tw);
+        apply_h<P, 2, MIXED>(a, b, pr.x, t, item, hp);
+        inv2x_from<P, CP, Lay, Geo<P>::NST - 1>(a, b, sm, cp, t, tw);
+    }
+    if (live) {
+        float2* da = wout + item * wout_item_stride + (long long)pr.x * NY;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) da[t + e * T] = a[e];
+        if (pr.y != pr.x) {
+            float2* db = wout + item * wout_item_stride + (long long)pr.y * NY;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) db[t + e * T] = b[e];
+        }
+    }
+}
+
+// Shared-source z-stack: the forward column transform of the source is computed once and kept
+// in registers; for each plane the kernel multiplies a copy by that plane's transfer function,
+// transforms it back and writes the plane (Section "Three-dimensional diffraction calculations":
+// a stack of 2-D diffractions of one source).
+template <int P, int C>
+__global__ void __launch_bounds__(C * (P / 16), col_min_blocks<P>())
+k_col_stack(const float2* __restrict__ win, float2* __restrict__ wout, long long wout_item_stride, int nplanes,
+            const float4* __restrict__ tw, const HParams hp) {
+    pdl_wait();
+    constexpr int T = P / 16, NY = P / 2;
+    using Lay = PadLayout<P, C>;
+    extern __shared__ float2 sm[];
+    const int t = threadIdx.x % T, c = threadIdx.x / T;
+    const int col = blockIdx.x * C + c;
+    const float2* src = win + (long long)col * NY;
+    float2 spec[16];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) spec[e] = src[t + e * T];
+#pragma unroll
+    for (int e = 8; e < 16; ++e) spec[e] = make_float2(0.f, 0.f);
+    const TwTable<P> twt{tw, t};
+    fwd_from<P, C, Lay, 0, 8, 0>(spec, sm, c, t, twt);
+#pragma unroll 1
+    for (int z = 0; z < nplanes; ++z) {
+        float2 v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = spec[e];
+        apply_h<P, 1>(v, v, col, t, z, hp);
+        inv_from<P, C, Lay, Geo<P>::NST - 1, 0, 0>(v, sm, c, t, twt);
+        float2* dst = wout + z * wout_item_stride + (long long)col * NY;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[t + e * T] = v[e];
+    }
+}
+
+
+template <int P, bool MIXED>
+static cudaError_t col_impl_t(const float2* win, long long win_item_stride, float2* wout,
+                              long long wout_item_stride, int px, int items, const float4* tw,
+                              const HParams& hp, cudaStream_t st) {
+    constexpr int T = P / 16;
+    cudaError_t e;
+    if (hp.asym) {   // H(kx) != H(-kx): one column per transform
+        constexpr int C = cols_per_block<P>();
+        if (px % C != 0) return cudaErrorInvalidValue;
+        const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
+        if ((e = kernel_setup<k_col<P, C, MIXED>>(smem, C * T, nullptr))) return e;
+        e = pdl_launch(k_col<P, C, MIXED>, dim3(px / C, items), dim3(C * T), smem, st, win, win_item_stride, wout,
+                       wout_item_stride, tw, hp);
+        if (e != cudaSuccess) return e;
+    } else if constexpr (col_paired<P>()) {
+        constexpr int CP = cols_per_block<P>();
+        if (hp.npairs != px / 2 + 1 || !hp.pairs) return cudaErrorInvalidValue;
+        const size_t smem = (size_t)colp_smem_words<P, CP>() * sizeof(float2);
+        int resident = 0;
+        if ((e = kernel_setup<k_colp<P, CP, MIXED>>(smem, CP * T, &resident))) return e;
+        const unsigned blocks = (unsigned)((hp.npairs + CP - 1) / CP);
+        e = pdl_launch(k_colp<P, CP, MIXED>, dim3(items, blocks), dim3(CP * T), smem, st, win, win_item_stride, wout,
+                       wout_item_stride, tw, hp, resident);
+        if (e != cudaSuccess) return e;
+    } else {
+        constexpr int C = cols_per_block<P>();
+        if (px % C != 0) return cudaErrorInvalidValue;
+        const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
+        if ((e = kernel_setup<k_col<P, C, MIXED>>(smem, C * T, nullptr))) return e;
+        e = pdl_launch(k_col<P, C, MIXED>, dim3(px / C, items), dim3(C * T), smem, st, win, win_item_stride, wout,
+                       wout_item_stride, tw, hp);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t col_impl(const float2* win, long long win_item_stride, float2* wout,
+                            long long wout_item_stride, int px, int items, const float4* tw,
+                            const HParams& hp, cudaStream_t st) {
+    return hp.items ? col_impl_t<P, true>(win, win_item_stride, wout, wout_item_stride, px, items, tw, hp, st)
+                    : col_impl_t<P, false>(win, win_item_stride, wout, wout_item_stride, px, items, tw, hp, st);
+}
+
+template <int P>
+static cudaError_t col_stack_impl(const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
+                                  const float4* tw, const HParams& hp, cudaStream_t st) {
+    constexpr int C = cols_per_block<P>();
+    constexpr int T = P / 16;
+    if (px % C != 0) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
+    cudaError_t e;
+    if ((e = kernel_setup<k_col_stack<P, C>>(smem, C * T, nullptr))) return e;
+    return pdl_launch(k_col_stack<P, C>, dim3(px / C), dim3(C * T), smem, st, win, wout, wout_item_stride, planes, tw, hp);
+}
+
+// Launchers of the sizes each translation unit instantiates (cwo_cols_a/b/c.cu: P <= 512,
+// P = 1024 and 2048, P = 4096 and 8192), so that the kernels compile in parallel.
+cudaError_t launch_col_a(int py, const float2* win, long long win_item_stride, float2* wout, long long wout_item_stride,
+                         int px, int items, const float4* tw, const HParams& hp, cudaStream_t st);
+cudaError_t launch_col_b(int py, const float2* win, long long win_item_stride, float2* wout, long long wout_item_stride,
+                         int px, int items, const float4* tw, const HParams& hp, cudaStream_t st);
+cudaError_t launch_col_c(int py, const float2* win, long long win_item_stride, float2* wout, long long wout_item_stride,
+                         int px, int items, const float4* tw, const HParams& hp, cudaStream_t st);
+cudaError_t launch_col_stack_a(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
+                               const float4* tw, const HParams& hp, cudaStream_t st);
+cudaError_t launch_col_stack_b(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
+                               const float4* tw, const HParams& hp, cudaStream_t st);
+cudaError_t launch_col_stack_c(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
+                               const float4* tw, const HParams& hp, cudaStream_t st);
+
+}  // namespace cwo
