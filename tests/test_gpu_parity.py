@@ -183,16 +183,19 @@ def test_asm_2048_full(cwo):
 
 
 @pytest.mark.slow
-def test_asm_2048_batch16_as_benchmarked(cwo):
+@pytest.mark.parametrize("cached", [True, False], ids=["once_h", "recalc_h"])
+def test_asm_2048_batch16_as_benchmarked(cwo, cached):
     # the benchmark's launch configuration: one batched call of 16 fields of 2048^2 (each field a
-    # random phase rotation of one random field), persistent row passes over 16 x 512 row groups;
-    # two sampled items against the oracle, every item against the first up to its rotation
+    # random phase rotation of one random field), persistent row passes over 16 x 512 row groups,
+    # the column pass's item-fastest grid, with the transfer function materialised per plan (the
+    # headline) or evaluated per element; two sampled items against the oracle, every item
+    # against the first up to its rotation
     import torch
     n, b = 2048, 16
     base = synth.random_field(n, seed=1000)
     rot = np.exp(2j * np.pi * synth.rng(5).random(b))
     x = torch.from_numpy((base[None] * rot[:, None, None]).astype(np.complex64)).cuda()
-    plan = cwo.Plan(n, n, 10e-6, 10e-6, 633e-9, 0.05, cwo.ANGULAR)
+    plan = cwo.Plan(n, n, 10e-6, 10e-6, 633e-9, 0.05, cwo.ANGULAR, cwo.FLAG_CACHE_H if cached else 0)
     plan.reserve(b)
     y = plan.propagate_batch(x)
     plan.check()
