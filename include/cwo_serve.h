@@ -81,7 +81,9 @@ cwo_status cwo_server_admit(int queued, int capacity, size_t in_use, size_t budg
 /*
  * Queue one request; *ticket identifies it.  The request is checked on the host first (size
  * served, type, parameters, one field within the budget, field and out device memory of the
- * server's device holding n*n complex64 values); on failure nothing is queued.
+ * server's device holding n*n complex64 values); on failure nothing is queued.  The server keeps
+ * a small record (~70 bytes) of every submitted request until it is destroyed, so that
+ * cwo_server_done answers for any ticket; an open-loop run keeps none of its own.
  */
 cwo_status cwo_server_submit(cwo_server* srv, const cwo_request* req, long long* ticket);
 

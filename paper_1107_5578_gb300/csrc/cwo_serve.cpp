@@ -367,6 +367,7 @@ cwo_status cwo_server_run(cwo_server* srv, const cwo_request* reqs, int nreq, do
         done += d;
     }
     for (int i = 0; i < nreq; ++i) t_done[i] = srv->tickets[base + i].t_done;
+    srv->tickets.resize(base);   // the run's own records: never handed out, all completed
     return CWO_OK;
 }
 
