@@ -121,12 +121,9 @@ bool line_stack_supported(int p);
 cudaError_t launch_line_stack(int p, const float2* in, const CUtensorMap* omap, int lines, int planes, const float2* h,
                               long long h_item_stride, int conj, float scale, const float4* tw, int* status,
                               cudaStream_t st);
-// out / out_item_stride: the same destination as omap as a plain pointer ([items][P/2][lines]); when
-// it is 16-byte aligned the pair form (P >= 128) stores through it and omap is not used
-cudaError_t launch_line_conv(int p, const float2* in, long long in_item_stride, const CUtensorMap* omap, float2* out,
-                             long long out_item_stride, int lines, int items, const float2* h, long long h_item_stride,
-                             int conj, float scale, const float4* tw, int* status, const float2* pre,
-                             const float2* post, cudaStream_t st);
+cudaError_t launch_line_conv(int p, const float2* in, long long in_item_stride, const CUtensorMap* omap, int lines,
+                             int items, const float2* h, long long h_item_stride, int conj, float scale,
+                             const float4* tw, int* status, const float2* pre, const float2* post, cudaStream_t st);
 cudaError_t launch_fourier_rows(int px, const float2* in, long long in_item_stride, const CUtensorMap* wmap, int ny,
                                 int items, const float2* pre_x, const float2* pre_y, const float4* tw, cudaStream_t st);
 cudaError_t launch_fourier_cols(int py, const float2* win, long long win_item_stride, float2* out, long long out_item_stride,

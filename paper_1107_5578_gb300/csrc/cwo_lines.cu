@@ -441,10 +441,10 @@ static cudaError_t line_stack_impl(const float2* in, const CUtensorMap* omap, in
 }
 
 template <int P, bool FAC>
-static cudaError_t line_conv_impl(const float2* in, long long in_item_stride, const CUtensorMap* omap, float2* out,
-                                  long long out_item_stride, int lines, int items, const float2* h,
-                                  long long h_item_stride, int conj, float scale, const float4* tw, int* status,
-                                  const float2* pre, const float2* post, cudaStream_t st) {
+static cudaError_t line_conv_impl(const float2* in, long long in_item_stride, const CUtensorMap* omap, int lines,
+                                  int items, const float2* h, long long h_item_stride, int conj, float scale,
+                                  const float4* tw, int* status, const float2* pre, const float2* post,
+                                  cudaStream_t st) {
     constexpr int R = line_rows<P>();
     constexpr int T = P / 16;
     if (lines % R || items < 1 || items > 65535) return cudaErrorInvalidValue;
@@ -503,14 +503,13 @@ cudaError_t launch_line_stack(int p, const float2* in, const CUtensorMap* omap, 
     }
 }
 
-cudaError_t launch_line_conv(int p, const float2* in, long long in_item_stride, const CUtensorMap* omap, float2* out,
-                             long long out_item_stride, int lines, int items, const float2* h, long long h_item_stride,
-                             int conj, float scale, const float4* tw, int* status, const float2* pre,
-                             const float2* post, cudaStream_t st) {
+cudaError_t launch_line_conv(int p, const float2* in, long long in_item_stride, const CUtensorMap* omap, int lines,
+                             int items, const float2* h, long long h_item_stride, int conj, float scale,
+                             const float4* tw, int* status, const float2* pre, const float2* post, cudaStream_t st) {
     if (!pre != !post) return cudaErrorInvalidValue;
     switch (p) {
-#define CASE(P) case P: return pre ? line_conv_impl<P, true>(in, in_item_stride, omap, out, out_item_stride, lines, items, h, h_item_stride, conj, scale, tw, status, pre, post, st) \
-                               : line_conv_impl<P, false>(in, in_item_stride, omap, out, out_item_stride, lines, items, h, h_item_stride, conj, scale, tw, status, nullptr, nullptr, st);
+#define CASE(P) case P: return pre ? line_conv_impl<P, true>(in, in_item_stride, omap, lines, items, h, h_item_stride, conj, scale, tw, status, pre, post, st) \
+                               : line_conv_impl<P, false>(in, in_item_stride, omap, lines, items, h, h_item_stride, conj, scale, tw, status, nullptr, nullptr, st);
         CASE(32) CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024) CASE(2048) CASE(4096) CASE(8192)
 #undef CASE
         default: return cudaErrorInvalidValue;

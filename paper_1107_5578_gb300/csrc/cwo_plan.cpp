@@ -543,8 +543,8 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
             (e = cwo::launch_line_stack(p->px, fin, &p->wmap_s, p->ny, batch, hp.hx, hp.x_item_stride, hp.conj,
                                         (float)(1.0 / p->px), p->tw_x, p->status, s)) ||
             (e = mark(1)) ||
-            (e = cwo::launch_line_conv(p->py, p->scratch, field, &omap, fout, field, p->nx, batch, hp.hy, hp.y_item_stride,
-                                       hp.conj, (float)(1.0 / p->py), p->tw_y, p->status, nullptr, nullptr, s)) ||
+            (e = cwo::launch_line_conv(p->py, p->scratch, field, &omap, p->nx, batch, hp.hy, hp.y_item_stride, hp.conj,
+                                       (float)(1.0 / p->py), p->tw_y, p->status, nullptr, nullptr, s)) ||
             (e = mark(2)) || (e = mark(3)))
             return cuda_fail(e, "separable Fresnel stack launch");
         return CWO_OK;
@@ -565,12 +565,11 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
             return cuda_fail(e, "tensor map of the output");
         const long long istr = in_stride ? in_stride : field;
         if ((e = mark(0)) ||
-            (e = cwo::launch_line_conv(p->px, fin, istr, &p->wmap_s, p->scratch, field, p->ny, batch, hp.hx,
-                                       hp.x_item_stride, hp.conj, (float)(1.0 / p->px), p->tw_x, p->status, prex, postx,
-                                       s)) ||
+            (e = cwo::launch_line_conv(p->px, fin, istr, &p->wmap_s, p->ny, batch, hp.hx, hp.x_item_stride, hp.conj,
+                                       (float)(1.0 / p->px), p->tw_x, p->status, prex, postx, s)) ||
             (e = mark(1)) ||
-            (e = cwo::launch_line_conv(p->py, p->scratch, field, &omap, fout, field, p->nx, batch, hp.hy, hp.y_item_stride,
-                                       hp.conj, (float)(1.0 / p->py), p->tw_y, p->status, prey, posty, s)) ||
+            (e = cwo::launch_line_conv(p->py, p->scratch, field, &omap, p->nx, batch, hp.hy, hp.y_item_stride, hp.conj,
+                                       (float)(1.0 / p->py), p->tw_y, p->status, prey, posty, s)) ||
             (e = mark(2)) || (e = mark(3)))
             return cuda_fail(e, "separable Fresnel launch");
         return CWO_OK;
