@@ -103,8 +103,8 @@ template <int P>
 __host__ __device__ constexpr int line_stage_stride() { return P / 2 + 4; }
 
 // exchange / tile region of the persistent form: the pair layout of the 128-bit exchanges
-// (P >= 128) or the padded layout, and the dense [position][line] tile, which aliases it
-// (the largest of the three, so that one staging offset serves every persistent line kernel)
+// (P >= 128) or the padded layout, and the dense [position][line] tile, which aliases it (the
+// larger of the two)
 template <int P, int R>
 __host__ __device__ constexpr size_t line_p_xwords() {
     return 2 * (size_t)PairLayout<P, (R / 2 > 0 ? R / 2 : 1)>::SLOTS > line_smem_words<P, R>()
@@ -342,20 +342,74 @@ k_line_pair(const float2* __restrict__ in, long long in_item_stride, const __gri
 
 // Shared-source z-stack, first pass: each source line is transformed once and its spectrum kept in
 // registers; for every plane j it is multiplied by that plane's axis table, transformed back and
-// stored into plane j's intermediate (item j of omap).  The second pass is k_line_conv_p over the
+// stored into plane j's intermediate (item j of omap).  The second pass is the line pass over the
 // planes.  One line per thread (spectrum and working copy: 32 values), R lines per group as in
-// line_rows, persistent with staged bulk loads as k_line_conv_p.
+// line_rows (interleaved over the lanes), persistent with staged bulk loads as k_line_conv_p.
+// The exchanges take one barrier each (warp-wide where the threads of one block of the earlier
+// stage, R lines of them, fit in a warp), and the kept half goes to one of two tiles of its own,
+// so that a plane waits only for the TMA store issued two planes before it.  Per plane: the
+// exchange into stage 0 (CTA-wide) and the barrier after the tile write, which also separates
+// this plane's last exchange reads from the next plane's first exchange writes.
+template <int P, int R>
+__host__ __device__ constexpr size_t stack_x_words() {
+    return ((size_t)PadLayout<P, R>::WORDS + 127) / 128 * 128;
+}
+template <int P, int R>
+__host__ __device__ constexpr size_t stack_smem_bytes() {
+    return (stack_x_words<P, R>() + 2 * (size_t)R * (P / 2) + (size_t)R * line_stage_stride<P>()) * sizeof(float2) +
+           sizeof(uint64_t);
+}
+
+template <int P, int R, int S>
+__device__ __forceinline__ void stack_sync() {
+    if constexpr (Geo<P>::stride(S) * R <= 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <int P, int R, int SW, int SR>
+__device__ __forceinline__ void stack_xch(float2* __restrict__ sm, int r, int t, float2 (&v)[16]) {
+    using Lay = PadLayout<P, R>;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) sm[Lay::addr(r, stage_pos<P, SW>(t, e))] = v[e];
+    stack_sync<P, R, (SW < SR ? SW : SR)>();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = sm[Lay::addr(r, stage_pos<P, SR>(t, e))];
+}
+
+template <int P, int R, int S>
+__device__ __forceinline__ void stack_fwd_from(float2 (&v)[16], float2* __restrict__ sm, int r, int t,
+                                               const TwTable<P>& tw) {
+    stage_butterflies<P, S, false, (S == 0 ? 8 : 16)>(v);
+    if constexpr (S < Geo<P>::NST - 1) {
+        tw.template apply<S, false>(v);
+        stack_xch<P, R, S, S + 1>(sm, r, t, v);
+        stack_fwd_from<P, R, S + 1>(v, sm, r, t, tw);
+    }
+}
+
+template <int P, int R, int S>
+__device__ __forceinline__ void stack_inv_from(float2 (&v)[16], float2* __restrict__ sm, int r, int t,
+                                               const TwTable<P>& tw) {
+    if constexpr (S < Geo<P>::NST - 1) tw.template apply<S, true>(v);
+    stage_butterflies<P, S, true, 16>(v);
+    if constexpr (S > 0) {
+        stack_xch<P, R, S, S - 1>(sm, r, t, v);
+        stack_inv_from<P, R, S - 1>(v, sm, r, t, tw);
+    }
+}
+
 template <int P, int R>
 __global__ void __launch_bounds__(R * (P / 16), 1)
 k_line_stack_p(const float2* __restrict__ in, const __grid_constant__ CUtensorMap omap, const float2* __restrict__ h,
                long long h_item_stride, int planes, int conj, float scale, const float4* __restrict__ tw,
                int groups, int* status) {
+    static_assert(Geo<P>::NST >= 2 && Geo<P>::stride(0) * R > 32, "the exchange into stage 0 is CTA-wide");
     pdl_wait();
     constexpr int T = P / 16, N = P / 2, NT = R * T, SST = line_stage_stride<P>();
     constexpr int BOX = N < kTmaBoxCols ? N : kTmaBoxCols;
-    using Lay = PadLayout<P, R>;
     extern __shared__ __align__(1024) float2 sm[];
-    float2* stage = sm + line_p_xwords<P, R>();
+    float2* tiles = sm + stack_x_words<P, R>();
+    float2* stage = tiles + 2 * R * N;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(stage + R * SST);
     const int r = threadIdx.x % R, t = threadIdx.x / R;
     auto issue = [&](int g) {   // thread 0: the R source lines of group g into the staging buffer
@@ -371,6 +425,7 @@ k_line_stack_p(const float2* __restrict__ in, const __grid_constant__ CUtensorMa
     __syncthreads();
     const TwTable<P> twt{tw, t};
     unsigned parity = 0;
+    int np = 0;   // planes stored by this CTA so far: plane tiles alternate
 #pragma unroll 1
     for (int g = blockIdx.x; g < groups; g += gridDim.x, parity ^= 1u) {
         const bool ok = mbar_wait_bounded(mbar, parity, status);
@@ -382,16 +437,12 @@ k_line_stack_p(const float2* __restrict__ in, const __grid_constant__ CUtensorMa
         fence_proxy_async_smem();   // these reads of the staging buffer precede the next bulk copy into it
         if (__syncthreads_or(!ok)) break;                                // a copy did not land
         if (threadIdx.x == 0 && g + (int)gridDim.x < groups) issue(g + gridDim.x);
-        stage_butterflies<P, 0, false, 8>(spec);
-        if constexpr (Geo<P>::NST > 1) twt.template apply<0, false>(spec);
-        if (threadIdx.x == 0) tma_store_wait_read();                      // previous tile read out
-        __syncthreads();
-        if constexpr (Geo<P>::NST > 1) {
-            exchange<P, R, Lay, 0, 1, 0, 0>(sm, r, t, spec);
-            fwd_from<P, R, Lay, 1, 8, 0>(spec, sm, r, t, twt);
-        }
+        stack_fwd_from<P, R, 0>(spec, sm, r, t, twt);
 #pragma unroll 1
-        for (int j = 0; j < planes; ++j) {
+        for (int j = 0; j < planes; ++j, ++np) {
+            float2* tile = tiles + (np & 1) * R * N;
+            // the store of two planes ago read its tile; the CTA-wide exchange below publishes it
+            if (threadIdx.x == 0) tma_store_wait_read_1();
             float2 v[16];
             const float2* hh = h + j * h_item_stride + t;
 #pragma unroll
@@ -399,18 +450,14 @@ k_line_stack_p(const float2* __restrict__ in, const __grid_constant__ CUtensorMa
                 const float2 w = __ldg(hh + e * T);
                 v[e] = conj ? cmulc(spec[e], w) : cmul(spec[e], w);
             }
-            if (j > 0) {   // the previous plane's tile (which aliases the exchange region) read out
-                if (threadIdx.x == 0) tma_store_wait_read();
-                __syncthreads();
-            }
-            inv_from<P, R, Lay, Geo<P>::NST - 1, 0, 0>(v, sm, r, t, twt);
+            stack_inv_from<P, R, Geo<P>::NST - 1>(v, sm, r, t, twt);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) sm[e * NT + threadIdx.x] = cscale(v[e], scale);
+            for (int e = 0; e < 8; ++e) tile[e * NT + threadIdx.x] = cscale(v[e], scale);
             fence_proxy_async_smem();
             __syncthreads();
             if (threadIdx.x == 0) {
 #pragma unroll 1
-                for (int bx = 0; bx < N / BOX; ++bx) tma_store_3d(&omap, sm + bx * BOX * R, g * R, bx * BOX, j);
+                for (int bx = 0; bx < N / BOX; ++bx) tma_store_3d(&omap, tile + bx * BOX * R, g * R, bx * BOX, j);
                 tma_store_commit();
             }
         }
@@ -428,7 +475,7 @@ static cudaError_t line_stack_impl(const float2* in, const CUtensorMap* omap, in
         return cudaErrorNotSupported;
     } else {
         if (lines % R || planes < 1 || !status || (uintptr_t)in % 16) return cudaErrorInvalidValue;
-        const size_t smem = line_p_smem_bytes<P, R>();
+        const size_t smem = stack_smem_bytes<P, R>();
         int resident = 0;
         cudaError_t e = kernel_setup<k_line_stack_p<P, R>>(smem, R * T, &resident);
         if (e != cudaSuccess) return e;
