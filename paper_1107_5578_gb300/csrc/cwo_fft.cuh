@@ -377,6 +377,56 @@ __device__ __forceinline__ void xsync(int cp) {
     }
 }
 
+// The same exchanges for R transforms of one value per thread, interleaved over the lanes
+// (thread = r + R t, PadLayout<P, R>), all of the CTA's threads in step: a stage-S block is
+// stride(S) threads of each of the R transforms, i.e. stride(S) * R consecutive lanes, so the
+// barrier is warp-wide where that fits in a warp and CTA-wide otherwise.
+template <int P, int R, int S>
+__device__ __forceinline__ void xsync_r() {
+    if constexpr (Geo<P>::stride(S) * R <= 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <int P, int R, int SW, int SR>
+__device__ __forceinline__ void xch1(float2* __restrict__ sm, int r, int t, float2 (&v)[16]) {
+    using Lay = PadLayout<P, R>;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) sm[Lay::addr(r, stage_pos<P, SW>(t, e))] = v[e];
+    xsync_r<P, R, (SW < SR ? SW : SR)>();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = sm[Lay::addr(r, stage_pos<P, SR>(t, e))];
+}
+
+// forward DIF from stage S to the end / adjoint from stage S down to stage 0 (or, for
+// inv1_to_stage0, down to and including the exchange into stage 0), with xch1 exchanges
+template <int P, int R, int S, int NZ0, class Tw>
+__device__ __forceinline__ void fwd1_from(float2 (&v)[16], float2* __restrict__ sm, int r, int t, const Tw& tw) {
+    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(v);
+    if constexpr (S < Geo<P>::NST - 1) {
+        tw.template apply<S, false>(v);
+        xch1<P, R, S, S + 1>(sm, r, t, v);
+        fwd1_from<P, R, S + 1, NZ0>(v, sm, r, t, tw);
+    }
+}
+
+template <int P, int R, int S, class Tw>
+__device__ __forceinline__ void inv1_from(float2 (&v)[16], float2* __restrict__ sm, int r, int t, const Tw& tw) {
+    if constexpr (S < Geo<P>::NST - 1) tw.template apply<S, true>(v);
+    stage_butterflies<P, S, true, 16>(v);
+    if constexpr (S > 0) {
+        xch1<P, R, S, S - 1>(sm, r, t, v);
+        inv1_from<P, R, S - 1>(v, sm, r, t, tw);
+    }
+}
+
+template <int P, int R, int S, class Tw>
+__device__ __forceinline__ void inv1_to_stage0(float2 (&v)[16], float2* __restrict__ sm, int r, int t, const Tw& tw) {
+    if constexpr (S < Geo<P>::NST - 1) tw.template apply<S, true>(v);
+    stage_butterflies<P, S, true, 16>(v);
+    xch1<P, R, S, S - 1>(sm, r, t, v);
+    if constexpr (S > 1) inv1_to_stage0<P, R, S - 1>(v, sm, r, t, tw);
+}
+
 template <int P, int CP, class Lay, int SW, int SR>
 __device__ __forceinline__ void xch2(float2* __restrict__ sm, int cp, int t, float2 (&a)[16], float2 (&b)[16]) {
 #pragma unroll

@@ -360,44 +360,6 @@ __host__ __device__ constexpr size_t stack_smem_bytes() {
            sizeof(uint64_t);
 }
 
-template <int P, int R, int S>
-__device__ __forceinline__ void stack_sync() {
-    if constexpr (Geo<P>::stride(S) * R <= 32) __syncwarp();
-    else __syncthreads();
-}
-
-template <int P, int R, int SW, int SR>
-__device__ __forceinline__ void stack_xch(float2* __restrict__ sm, int r, int t, float2 (&v)[16]) {
-    using Lay = PadLayout<P, R>;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) sm[Lay::addr(r, stage_pos<P, SW>(t, e))] = v[e];
-    stack_sync<P, R, (SW < SR ? SW : SR)>();
-#pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = sm[Lay::addr(r, stage_pos<P, SR>(t, e))];
-}
-
-template <int P, int R, int S>
-__device__ __forceinline__ void stack_fwd_from(float2 (&v)[16], float2* __restrict__ sm, int r, int t,
-                                               const TwTable<P>& tw) {
-    stage_butterflies<P, S, false, (S == 0 ? 8 : 16)>(v);
-    if constexpr (S < Geo<P>::NST - 1) {
-        tw.template apply<S, false>(v);
-        stack_xch<P, R, S, S + 1>(sm, r, t, v);
-        stack_fwd_from<P, R, S + 1>(v, sm, r, t, tw);
-    }
-}
-
-template <int P, int R, int S>
-__device__ __forceinline__ void stack_inv_from(float2 (&v)[16], float2* __restrict__ sm, int r, int t,
-                                               const TwTable<P>& tw) {
-    if constexpr (S < Geo<P>::NST - 1) tw.template apply<S, true>(v);
-    stage_butterflies<P, S, true, 16>(v);
-    if constexpr (S > 0) {
-        stack_xch<P, R, S, S - 1>(sm, r, t, v);
-        stack_inv_from<P, R, S - 1>(v, sm, r, t, tw);
-    }
-}
-
 template <int P, int R>
 __global__ void __launch_bounds__(R * (P / 16), 1)
 k_line_stack_p(const float2* __restrict__ in, const __grid_constant__ CUtensorMap omap, const float2* __restrict__ h,
@@ -437,7 +399,7 @@ k_line_stack_p(const float2* __restrict__ in, const __grid_constant__ CUtensorMa
         fence_proxy_async_smem();   // these reads of the staging buffer precede the next bulk copy into it
         if (__syncthreads_or(!ok)) break;                                // a copy did not land
         if (threadIdx.x == 0 && g + (int)gridDim.x < groups) issue(g + gridDim.x);
-        stack_fwd_from<P, R, 0>(spec, sm, r, t, twt);
+        fwd1_from<P, R, 0, 8>(spec, sm, r, t, twt);
 #pragma unroll 1
         for (int j = 0; j < planes; ++j, ++np) {
             float2* tile = tiles + (np & 1) * R * N;
@@ -450,7 +412,7 @@ k_line_stack_p(const float2* __restrict__ in, const __grid_constant__ CUtensorMa
                 const float2 w = __ldg(hh + e * T);
                 v[e] = conj ? cmulc(spec[e], w) : cmul(spec[e], w);
             }
-            stack_inv_from<P, R, Geo<P>::NST - 1>(v, sm, r, t, twt);
+            inv1_from<P, R, Geo<P>::NST - 1>(v, sm, r, t, twt);
 #pragma unroll
             for (int e = 0; e < 8; ++e) tile[e * NT + threadIdx.x] = cscale(v[e], scale);
             fence_proxy_async_smem();

@@ -182,8 +182,9 @@ k_row_fwd_p(const float2* __restrict__ in, long long in_item_stride, const __gri
         if (threadIdx.x == 0) tma_store_wait_read();
         __syncthreads();
         if constexpr (Geo<P>::NST > 1) {
-            exchange<P, R, PadLayout<P, R>, 0, 1, 0, 0>(sm, r, t, v);
-            fwd_from<P, R, PadLayout<P, R>, 1, 8, 0>(v, sm, r, t, twt);
+            xch1<P, R, 0, 1>(sm, r, t, v);
+            fwd1_from<P, R, 1, 8>(v, sm, r, t, twt);
+            __syncthreads();   // every exchange read done before the tile (which aliases the region) is written
         }
 #pragma unroll
         for (int e = 0; e < 16; ++e) sm[e * NT + threadIdx.x] = v[e];
@@ -273,9 +274,9 @@ k_row_fwd_c(const float2* __restrict__ in, long long in_item_stride, const __gri
         twt.template apply<0, false>(v);
         if (threadIdx.x == 0) tma_store_wait_read();     // this CTA's previous tile read out
         __syncthreads();
-        exchange<P, R, PadLayout<P, R>, 0, 1, 0, 0>(sm, r, t, v);
-        fwd_from<P, R, PadLayout<P, R>, 1, 8, 0>(v, sm, r, t, twt);
-        cluster_sync();   // both exchange regions free; both previous tiles read out
+        xch1<P, R, 0, 1>(sm, r, t, v);
+        fwd1_from<P, R, 1, 8>(v, sm, r, t, twt);
+        cluster_sync();   // both exchange regions free (every exchange read done); both previous tiles read out
         const int row4 = 2 * (int)rank + r;
 #pragma unroll
         for (int e = 0; e < 16; ++e) {   // storage column e T + t lies in half e / 8
@@ -334,7 +335,7 @@ k_row_inv_p(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __re
 #pragma unroll
         for (int e = 0; e < 16; ++e) v[e] = sm[e * NT + threadIdx.x];
         if (__syncthreads_or(!ok)) break;          // a copy did not land: the status word says so
-        inv_to_stage0<P, R, PadLayout<P, R>, Geo<P>::NST - 1, 0, 0>(v, sm, r, t, twt);
+        inv1_to_stage0<P, R, Geo<P>::NST - 1>(v, sm, r, t, twt);
         fence_proxy_async_smem();                  // the exchange reads precede the next tile load
         __syncthreads();
         if (threadIdx.x == 0 && g + (int)gridDim.x < total_groups) issue(g + gridDim.x);
