@@ -70,15 +70,16 @@ k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restr
 // -kx.  H depends on kx only through kx^2 (both methods), so the transfer function is evaluated
 // (or loaded) once for both, and the twiddles of each stage are loaded once for both.  The
 // exchanges take one barrier each (warp-wide after the first stage) and move a pair's two values
-// at one position with one 128-bit access (P >= 128; P = 8192 keeps 64-bit accesses, which fit in
-// the registers without spilling).  The grid is (items, pair groups), item fastest, so that the
-// CTAs running at one time share few pair groups: the transfer-function values of a pair (the
+// at one position with one 128-bit access (P >= 128; at P = 8192 the 128-bit form measured 325
+// against 334 us per 4096^2 field for 64-bit accesses, with the transfer function cached).  The
+// grid is (items, pair groups), item fastest, so that the CTAs running at one time share few pair
+// groups: the transfer-function values of a pair (the
 // cached table of a once-calculation plan) are read from HBM once and from L2 by the other items.
 // Thread 0 prefetches into L2 the columns of the CTA that will take this CTA's place (`resident`
 // CTAs later in launch order).
 template <int P, int CP>
 constexpr int colp_smem_words() {
-    return (P >= 128 && P < 8192) ? 2 * PairLayout<P, CP>::SLOTS : PadLayout<P, 2 * CP>::WORDS;
+    return P >= 128 ? 2 * PairLayout<P, CP>::SLOTS : PadLayout<P, 2 * CP>::WORDS;
 }
 
 template <int P, int CP, bool MIXED>
@@ -120,7 +121,7 @@ k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __rest
     for (int e = 0; e < 8; ++e) { a[e] = sa[t + e * T]; b[e] = sb[t + e * T]; }
 #pragma unroll
     for (int e = 8; e < 16; ++e) { a[e] = make_float2(0.f, 0.f); b[e] = make_float2(0.f, 0.f); }
-    if constexpr (P >= 128 && P < 8192) {
+    if constexpr (P >= 128) {
         fwd2v_from<P, CP, 0, 8>(a, b, reinterpret_cast<float4*>(sm), cp, t, tw);
         apply_h<P, 2, MIXED>(a, b, pr.x, t, item, hp);
         inv2v_from<P, CP, Geo<P>::NST - 1>(a, b, reinterpret_cast<float4*>(sm), cp, t, tw);
