@@ -494,6 +494,18 @@ __device__ __forceinline__ void inv2v_from(float2 (&a)[16], float2 (&b)[16], flo
     }
 }
 
+// the same down to (and including) the exchange into stage 0; the caller applies the stage-0
+// twiddles and butterflies (the inverse row pass requests its next tile before them)
+template <int P, int CP, int S>
+__device__ __forceinline__ void inv2v_to_stage0(float2 (&a)[16], float2 (&b)[16], float4* __restrict__ sm, int cp,
+                                                int t, const float4* __restrict__ tw) {
+    if constexpr (S < Geo<P>::NST - 1) twiddle2<P, S, true>(a, b, tw, t);
+    stage_butterflies<P, S, true, 16>(a);
+    stage_butterflies<P, S, true, 16>(b);
+    xch2v<P, CP, S, S - 1>(sm, cp, t, a, b);
+    if constexpr (S > 1) inv2v_to_stage0<P, CP, S - 1>(a, b, sm, cp, t, tw);
+}
+
 template <int P, int CP, class Lay, int S, int NZ0>
 __device__ __forceinline__ void fwd2x_from(float2 (&a)[16], float2 (&b)[16], float2* __restrict__ sm, int cp, int t,
                                            const float4* __restrict__ tw) {

@@ -350,6 +350,75 @@ k_row_inv_p(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __re
 
 
 
+// Inverse, pair form (P = 8192): each thread transforms two rows of the group (2 cp and 2 cp + 1
+// of its CP = R / 2 pairs), which share every twiddle load, and moves both rows' values at one
+// position with one 128-bit access -- in the tile read (the tile [st][r] holds the pair at
+// st R + 2 cp, + 1) and in the exchanges (PairLayout, one barrier each).  Otherwise as
+// k_row_inv_p: one tile buffer aliasing the exchange region, the next group's tile requested after
+// the last exchange.  Measured per field against k_row_inv_p: 4096^2 159.6 against 171.5 us; at
+// 2048^2 (24.2 against 23.0 us) and 1024^2 (5.85 against 5.70) the half as many warps per SM cost
+// more than the shared twiddle loads save.
+template <int P, int CP>
+__host__ __device__ constexpr size_t row_inv_pp_words() {
+    return 2 * (size_t)PairLayout<P, CP>::SLOTS > (size_t)2 * CP * P ? 2 * (size_t)PairLayout<P, CP>::SLOTS
+                                                                       : (size_t)2 * CP * P;
+}
+
+template <int P, int CP, int EPI>
+__global__ void __launch_bounds__(CP * (P / 16), CP * (P / 16) >= 512 ? 1 : 2)
+k_row_inv_pp(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __restrict__ out,
+             long long out_item_stride, int groups_per_item, int total_groups, float scale,
+             const float4* __restrict__ tw, int* status, const Epilogue ep) {
+    pdl_wait();
+    constexpr int R = 2 * CP, T = P / 16, N = P / 2;
+    constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
+    static_assert(Geo<P>::NST >= 2 && P >= 128, "at least two stages, 128-bit pair exchanges");
+    extern __shared__ __align__(1024) float2 sm[];
+    float4* sx = reinterpret_cast<float4*>(sm);
+    const float4* tile = reinterpret_cast<const float4*>(sm);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + row_inv_pp_words<P, CP>());
+    const int t = CP == 1 ? (int)threadIdx.x : (int)threadIdx.x % T;
+    const int cp = CP == 1 ? 0 : (int)threadIdx.x / T;
+    auto issue = [&](int g) {   // thread 0: the R-row tile of group g
+        const int item = g / groups_per_item, y0 = (g % groups_per_item) * R;
+        mbar_arrive_expect_tx(mbar, (unsigned)(R * P * sizeof(float2)));
+#pragma unroll 1
+        for (int b = 0; b < P / BOX; ++b) tma_load_3d(sm + b * BOX * R, &wmap, mbar, y0, b * BOX, item + item_off);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        if ((int)blockIdx.x < total_groups) issue(blockIdx.x);
+    }
+    __syncthreads();
+    unsigned parity = 0;
+#pragma unroll 1
+    for (int g = blockIdx.x; g < total_groups; g += gridDim.x, parity ^= 1u) {
+        const bool ok = mbar_wait_bounded(mbar, parity, status);
+        float2 a[16], b[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const float4 q = tile[(e * T + t) * CP + cp];
+            a[e] = make_float2(q.x, q.y);
+            b[e] = make_float2(q.z, q.w);
+        }
+        if (__syncthreads_or(!ok)) break;          // a copy did not land: the status word says so
+        inv2v_to_stage0<P, CP, Geo<P>::NST - 1>(a, b, sx, cp, t, tw);
+        fence_proxy_async_smem();                  // the exchange reads precede the next tile load
+        __syncthreads();
+        if (threadIdx.x == 0 && g + (int)gridDim.x < total_groups) issue(g + gridDim.x);
+        twiddle2<P, 0, true>(a, b, tw, t);
+        stage_butterflies<P, 0, true, 16>(a);
+        stage_butterflies<P, 0, true, 16>(b);
+        const int item = g / groups_per_item, y0 = (g % groups_per_item) * R + 2 * cp;
+        const long long base = item * out_item_stride + (long long)y0 * N;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {   // crop: positions t + e T < N of rows y0 and y0 + 1
+            epilogue_store<EPI>(out, ep, base + t + e * T, t + e * T, y0, cscale(a[e], scale));
+            epilogue_store<EPI>(out, ep, base + N + t + e * T, t + e * T, y0 + 1, cscale(b[e], scale));
+        }
+    }
+}
+
 template <int P, bool PRE, bool BULK>
 static cudaError_t row_fwd_c_launch(const float2* in, long long in_item_stride, const CUtensorMap* wmap, int item_off,
                                     int ny, int items, const float4* tw, int* status, const Prefactor& pre,
@@ -419,6 +488,18 @@ static cudaError_t row_inv_impl_e(const CUtensorMap* wmap, int item_off, float2*
     constexpr int T = P / 16;
     const size_t smem = row_smem_words<P, R>() * sizeof(float2) + sizeof(uint64_t);   // tile + mbarrier
     if (ny % R) return cudaErrorInvalidValue;
+    if constexpr (P >= 8192 && R % 2 == 0) {
+        constexpr int CP = R / 2;
+        const size_t psmem = row_inv_pp_words<P, CP>() * sizeof(float2) + sizeof(uint64_t);
+        int resident = 0;
+        cudaError_t e = kernel_setup<k_row_inv_pp<P, CP, EPI>>(psmem, CP * T, &resident);
+        if (e != cudaSuccess) return e;
+        const int groups = (ny / R) * items;
+        const int grid = std::min(groups, resident);
+        if (grid > 0)
+            return pdl_launch(k_row_inv_pp<P, CP, EPI>, dim3(grid), dim3(CP * T), psmem, st, *wmap, item_off, out,
+                              out_item_stride, ny / R, groups, scale, tw, status, ep);
+    }
     if constexpr (kRowInvPersistent && P >= 512) {
         int resident = 0;
         cudaError_t e = kernel_setup<k_row_inv_p<P, R, EPI>>(smem, R * T, &resident);
