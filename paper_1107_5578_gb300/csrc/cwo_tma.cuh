@@ -59,6 +59,10 @@ __device__ __forceinline__ unsigned cluster_map(unsigned smem_addr, unsigned ran
 __device__ __forceinline__ void st_cluster(unsigned addr, float2 v) {
     asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" :: "r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
+__device__ __forceinline__ void st_cluster4(unsigned addr, float4 v) {   // addr 16-byte aligned
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" :: "r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
 // every thread of every CTA of the cluster arrives; release / acquire order the shared-memory
 // accesses before and after it across the cluster
 __device__ __forceinline__ void cluster_sync() {
