@@ -36,11 +36,11 @@ BYTES_PER_PROP = 80 * N * N          # 3 passes: 8N^2 + 16N^2 | 16N^2 + 16N^2 | 
 COL_BYTES_PER_PROP = 32 * N * N      # column pass: read + write the Ny x Px intermediate
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each pass at batch 16,
-# from one ncu capture of the current kernels (profiles/asm_2048_batch16_launches.md); scaled by
-# the batch (traffic grows in proportion to the fields processed).  The column pass reads the
-# 67 MB transfer-function table of the plan once per launch besides its 16 fields.
-NCU_TRAFFIC_B16 = {"row_fwd": 1555.59e6, "col_fwd_h_inv": 2151.98e6, "row_inv": 1600.07e6}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel at
+# batch 16, from one ncu capture of the current column kernel (profiles/asm_2048_batch16_launches.md);
+# scaled by the batch (traffic grows in proportion to the fields processed).  The column pass reads
+# the 67 MB transfer-function table of the plan once per launch besides its 16 fields.
+NCU_TRAFFIC_B16 = {"col_fwd_h_inv": 2151.98e6}
 
 
 def traffic_bytes(kernel, batch):
