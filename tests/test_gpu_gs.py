@@ -30,8 +30,9 @@ def _phase_ok(got, want_u, tol_rad=2e-4):
     return np.max(np.abs(d)) <= tol_rad, np.max(np.abs(np.abs(got) - 1.0))
 
 
-@pytest.mark.parametrize("n", [64, 256])
+@pytest.mark.parametrize("n", [64, 256, pytest.param(4096, marks=pytest.mark.slow)])
 def test_epilogue_steps(mods, n):
+    # 4096: the inverse row pass with a thread per pair of rows (P = 8192) and each epilogue
     torch, cwo, _ = mods
     amp, f0 = synth.gs_problem(n, seed=3)
     plan = cwo.Plan(n, n, 8e-6, 8e-6, 532e-9, 0.02, cwo.ANGULAR)

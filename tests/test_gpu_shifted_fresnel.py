@@ -100,3 +100,42 @@ def test_shifted_fresnel_two_passes_equal_three(cwo, case, adjoint):
     plan.check()
     plan.close()
     assert _rel(a, b) <= 1e-5
+
+
+@pytest.mark.slow
+def test_shifted_fresnel_large_lines_against_oracle(cwo):
+    # rows padded to 4096 and columns to 2048: the pair form of the line pass with the source and
+    # destination factors of both axes
+    import torch
+    nx, ny, dx0, dy0, lam, z = 2048, 1024, 6e-6, 6e-6, 532e-9, 0.25
+    prm = (9e-6, 4e-6, 20e-6, -30e-6, 600e-6, -300e-6)
+    u = synth.random_field(nx, seed=75, ny=ny)
+    plan = cwo.Plan(nx, ny, dx0, dy0, lam, z, shifted_fresnel=cwo.ShiftedFresnel(*prm))
+    assert plan.launches_per_call == 2
+    got = plan.propagate(torch.from_numpy(u.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+    plan.check()
+    plan.close()
+    want = oracle.shifted_fresnel(u.astype(np.complex64), dx0, dy0, prm[0], prm[1], lam, z, *prm[2:])
+    assert _rel(got, want) <= TOL
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_shifted_fresnel_4096_two_passes_equal_three(cwo, adjoint):
+    # 4096^2: the persistent line pass at P = 8192 with both factors against the three-pass method
+    # (an output off a 16-byte boundary), whose forward row pass multiplies by the source factors
+    # (the cluster kernel at P = 8192) and whose inverse row pass applies the destination factors
+    import torch
+    n, dx0, lam, z = 4096, 3.74e-6, 532e-9, 0.3
+    prm = (5e-6, 5e-6, 0.0, 0.0, 2e-3, -1e-3)
+    plan = cwo.Plan(n, n, dx0, dx0, lam, z, shifted_fresnel=cwo.ShiftedFresnel(*prm))
+    x = torch.from_numpy(synth.random_field(n, seed=76).astype(np.complex64)).cuda()
+    run = plan.adjoint if adjoint else plan.propagate
+    a = run(x).cpu().numpy().astype(np.complex128)
+    buf = torch.empty(n * n + 1, dtype=torch.complex64, device="cuda")
+    out = buf[1:].view(n, n)
+    run(x, out=out)
+    b = out.cpu().numpy().astype(np.complex128)
+    plan.check()
+    plan.close()
+    assert _rel(a, b) <= 1e-5
