@@ -7,7 +7,7 @@
 // (digit-reversed) order, the transfer function is applied in that order, and the inverse is the
 // exact adjoint of the forward stages (conjugate twiddles, inverse butterflies, stages in reverse),
 // which consumes digit-reversed input and returns natural order.  Between stages the values are
-// exchanged through shared memory with an XOR swizzle that keeps every access bank-conflict free.
+// exchanged through shared memory in padded layouts that keep every access bank-conflict free.
 //
 // Stage s works on sub-transforms of length L_s = P / 16^s with stride S_s = L_s / radix(s).
 //   stage s < NST-1 : thread t owns butterfly t: block b = t / S_s, offset j = t % S_s, and its
@@ -186,22 +186,10 @@ CWO_HD int stage_pos(int t, int e) {
     }
 }
 
-// Shared-memory layouts of C transforms of length P.  Both keep every access of every stage
-// bank-conflict free when the C transforms are interleaved across a warp's lanes.
-//   SwzLayout: XOR swizzle of the low 4 position bits (no padding).
-//   PadLayout: one pad word per 16 positions plus a per-transform shift of 16/C words; the
-//              address of register e at any stage is a per-thread base plus a compile-time
-//              constant, so no per-element address arithmetic is left.
-template <int P, int C>
-CWO_HD int swz(int c, int pos) {
-    constexpr int K = C >= 16 ? 1 : 16 / C;
-    return c * P + (pos ^ (((pos >> 4) ^ (c * K)) & 15));
-}
-template <int P, int C>
-struct SwzLayout {
-    static constexpr int WORDS = C * P;
-    static CWO_HD int addr(int c, int pos) { return swz<P, C>(c, pos); }
-};
+// Shared-memory layout of C transforms of length P, bank-conflict free at every stage when the C
+// transforms are interleaved across a warp's lanes: one pad word per 16 positions plus a
+// per-transform shift of 16/C words; the address of register e at any stage is a per-thread base
+// plus a compile-time constant, so no per-element address arithmetic is left.
 template <int P, int C>
 struct PadLayout {
     static constexpr int R = P + P / 16 + (C <= 16 ? 16 / C : 1);
@@ -274,83 +262,6 @@ __device__ __forceinline__ void twiddle2(float2 (&a)[16], float2 (&b)[16], const
             a[2 * kp + 2] = INV ? cmulc(a[2 * kp + 2], w1) : cmul(a[2 * kp + 2], w1);
             b[2 * kp + 2] = INV ? cmulc(b[2 * kp + 2], w1) : cmul(b[2 * kp + 2], w1);
         }
-    }
-}
-
-// TwRegs: the twiddles of the first two stages held in registers for the life of a persistent
-// thread (they depend on t only), loaded once from the same table.
-template <int P>
-struct TwRegs {
-    static constexpr int NS = Geo<P>::NST - 1 < 2 ? Geo<P>::NST - 1 : 2;   // stages kept
-    float2 w[NS > 0 ? NS : 1][15];
-    const float4* __restrict__ tw;
-    int t;
-    __device__ __forceinline__ void load(const float4* __restrict__ table, int tt) {
-        tw = table;
-        t = tt;
-#pragma unroll
-        for (int s = 0; s < NS; ++s)
-#pragma unroll
-            for (int kp = 0; kp < 8; ++kp) {
-                const int SS = Geo<P>::stride(s);
-                const float4 q = __ldg(table + Geo<P>::tw_off(s) + kp * SS + (tt & (SS - 1)));
-                w[s][2 * kp] = make_float2(q.x, q.y);
-                if (kp < 7) w[s][2 * kp + 1] = make_float2(q.z, q.w);
-            }
-    }
-    template <int S, bool INV>
-    __device__ __forceinline__ void apply(float2 (&v)[16]) const {
-        if constexpr (S < NS) {
-#pragma unroll
-            for (int k = 1; k < 16; ++k) v[k] = INV ? cmulc(v[k], w[S][k - 1]) : cmul(v[k], w[S][k - 1]);
-        } else {
-            TwTable<P>{tw, t}.template apply<S, INV>(v);
-        }
-    }
-};
-
-// exchange of two transforms (indices c0, c0 + 1) held by the same thread
-template <int P, int C, class Lay, int SW, int SR, int PING, int XNUM>
-__device__ __forceinline__ void exchange2(float2* __restrict__ sm, int c0, int t, float2 (&a)[16], float2 (&b)[16]) {
-    float2* s = PING ? sm + (XNUM & 1) * Lay::WORDS : sm;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        s[Lay::addr(c0, stage_pos<P, SW>(t, e))] = a[e];
-        s[Lay::addr(c0 + 1, stage_pos<P, SW>(t, e))] = b[e];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        a[e] = s[Lay::addr(c0, stage_pos<P, SR>(t, e))];
-        b[e] = s[Lay::addr(c0 + 1, stage_pos<P, SR>(t, e))];
-    }
-    if (!PING) __syncthreads();
-}
-
-// forward DIF of two transforms sharing thread, twiddles and exchanges
-template <int P, int C, class Lay, int S, int NZ0, int PING>
-__device__ __forceinline__ void fwd2_from(float2 (&a)[16], float2 (&b)[16], float2* __restrict__ sm, int c0, int t,
-                                          const float4* __restrict__ tw) {
-    using G = Geo<P>;
-    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(a);
-    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(b);
-    if constexpr (S < G::NST - 1) {
-        twiddle2<P, S, false>(a, b, tw, t);
-        exchange2<P, C, Lay, S, S + 1, PING, S>(sm, c0, t, a, b);
-        fwd2_from<P, C, Lay, S + 1, NZ0, PING>(a, b, sm, c0, t, tw);
-    }
-}
-
-template <int P, int C, class Lay, int S, int PING, int XOFF>
-__device__ __forceinline__ void inv2_from(float2 (&a)[16], float2 (&b)[16], float2* __restrict__ sm, int c0, int t,
-                                          const float4* __restrict__ tw) {
-    using G = Geo<P>;
-    if constexpr (S < G::NST - 1) twiddle2<P, S, true>(a, b, tw, t);
-    stage_butterflies<P, S, true, 16>(a);
-    stage_butterflies<P, S, true, 16>(b);
-    if constexpr (S > 0) {
-        exchange2<P, C, Lay, S, S - 1, PING, XOFF + (G::NST - 1 - S)>(sm, c0, t, a, b);
-        inv2_from<P, C, Lay, S - 1, PING, XOFF>(a, b, sm, c0, t, tw);
     }
 }
 
@@ -555,18 +466,6 @@ __device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ s
         exchange<P, C, Lay, S, S - 1, PING, XOFF + (G::NST - 1 - S)>(sm, c, t, v);
         inv_from<P, C, Lay, S - 1, PING, XOFF>(v, sm, c, t, tw);
     }
-}
-
-// Adjoint stages from stage S down to (and including the exchange into) stage 0; the caller
-// applies the stage-0 twiddles and butterflies (the inverse row pass overlaps the next tile's
-// load with them).
-template <int P, int C, class Lay, int S, int PING, int XOFF, class Tw>
-__device__ __forceinline__ void inv_to_stage0(float2 (&v)[16], float2* __restrict__ sm, int c, int t, const Tw& tw) {
-    using G = Geo<P>;
-    if constexpr (S < G::NST - 1) tw.template apply<S, true>(v);
-    stage_butterflies<P, S, true, 16>(v);
-    exchange<P, C, Lay, S, S - 1, PING, XOFF + (G::NST - 1 - S)>(sm, c, t, v);
-    if constexpr (S > 1) inv_to_stage0<P, C, Lay, S - 1, PING, XOFF>(v, sm, c, t, tw);
 }
 
 #endif  // __CUDACC__

@@ -257,7 +257,7 @@ k_line_conv_p(const float2* __restrict__ in, long long in_item_stride, const __g
 template <int P> constexpr int line_pairs_per_block() { return line_rows<P>() / 2; }
 template <int P, int CP>
 constexpr int line_pair_smem_words() {
-    constexpr int x = (P >= 128 && P < 8192) ? 2 * PairLayout<P, CP>::SLOTS : PadLayout<P, 2 * CP>::WORDS;
+    constexpr int x = 2 * PairLayout<P, CP>::SLOTS;
     constexpr int tile = 2 * CP * (P / 2);
     return x > tile ? x : tile;
 }
@@ -268,7 +268,7 @@ k_line_pair(const float2* __restrict__ in, long long in_item_stride, const __gri
             const float2* __restrict__ h, long long h_item_stride, int conj, float scale,
             const float4* __restrict__ tw, const float2* __restrict__ pre, const float2* __restrict__ post,
             int resident) {
-    static_assert(P >= 128, "the pair form needs T >= 8");
+    static_assert(P >= 512 && P <= 4096, "the pair form serves 512 <= P <= 4096");
     pdl_wait();
     constexpr int T = P / 16, N = P / 2;
     extern __shared__ __align__(1024) float2 sm[];
@@ -309,16 +309,9 @@ k_line_pair(const float2* __restrict__ in, long long in_item_stride, const __gri
             b[e] = conj ? cmulc(b[e], w) : cmul(b[e], w);
         }
     };
-    if constexpr (P < 8192) {
-        fwd2v_from<P, CP, 0, 8>(a, b, reinterpret_cast<float4*>(sm), cp, t, tw);
-        mul_h();
-        inv2v_from<P, CP, Geo<P>::NST - 1>(a, b, reinterpret_cast<float4*>(sm), cp, t, tw);
-    } else {
-        using Lay = PadLayout<P, 2 * CP>;
-        fwd2x_from<P, CP, Lay, 0, 8>(a, b, sm, cp, t, tw);
-        mul_h();
-        inv2x_from<P, CP, Lay, Geo<P>::NST - 1>(a, b, sm, cp, t, tw);
-    }
+    fwd2v_from<P, CP, 0, 8>(a, b, reinterpret_cast<float4*>(sm), cp, t, tw);
+    mul_h();
+    inv2v_from<P, CP, Geo<P>::NST - 1>(a, b, reinterpret_cast<float4*>(sm), cp, t, tw);
     constexpr int R = 2 * CP, BOX = N < kTmaBoxCols ? N : kTmaBoxCols;
     __syncthreads();   // every exchange read done before the tile (which aliases the region) is written
 #pragma unroll
@@ -470,7 +463,7 @@ static cudaError_t line_conv_impl(const float2* in, long long in_item_stride, co
                           in_item_stride, *omap, h, h_item_stride, conj, scale, tw, pre, post, resident);
     }
     }
-    if constexpr (P >= 512) {
+    if constexpr (P >= 8192) {
     if (aligned && status) {
         const size_t smem = line_p_smem_bytes<P, R>();
         int resident = 0;
