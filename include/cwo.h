@@ -259,7 +259,10 @@ cwo_status cwo_propagate_epilogue(cwo_plan* plan, const void* in_c64, void* out_
  *   intensity <- |ASM(-z) field|^2                                   (if intensity != NULL)
  * field_c64 (in: the object field, amplitude times its initial phase; out: the kinoform),
  * amplitude and intensity are [batch][ny][nx] device buffers of the caller.  Each propagation is
- * the three-pass path with the constraint fused into its last pass (6 launches per iteration).
+ * the three-pass path with the constraint fused into its last pass; up to nx = 1024 the field stays
+ * in the plan's intermediate between propagations and one kernel turns from each propagation to
+ * the next (inverse row pass, constraint, forward row pass: 4 launches per iteration, the same
+ * values bit for bit), above it each propagation reads and writes the field (6 launches).
  * CWO_ERR_UNSUPPORTED for a Fresnel plan, CWO_ERR_INVALID_ARG for bad arguments. */
 cwo_status cwo_gs_run(cwo_plan* plan, const float* amplitude, void* field_c64, float* intensity, int batch,
                       int iterations, void* cuda_stream);

@@ -99,6 +99,12 @@ cudaError_t launch_row_fwd(int px, const float2* in, long long in_item_stride, c
 cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2* out, long long out_item_stride,
                            int ny, int items, float scale, const float4* tw, int* status, cudaStream_t st,
                            const Epilogue& ep = Epilogue());
+// The inverse row pass with an EPI_PHASE or EPI_AMPLITUDE constraint followed by the forward row
+// pass of the next propagation, in place on the intermediate through `wmap` (the forward pass's
+// map); field_item_stride indexes the constraint's amplitude [items][Ny][Nx].  64 <= Px <= 4096 (row_turn_supported: up to 2048).
+bool row_turn_supported(int px);
+cudaError_t launch_row_turn(int px, const CUtensorMap* wmap, int ny, int items, long long field_item_stride, float scale,
+                            const float4* tw, int* status, const Epilogue& ep, cudaStream_t st);
 // column pass of a shared-source z-stack: one forward transform per column, `planes` outputs
 cudaError_t launch_col_stack(int py, const float2* win, float2* wout, long long wout_item_stride, int px, int planes,
                              const float4* tw, const HParams& hp, cudaStream_t st);

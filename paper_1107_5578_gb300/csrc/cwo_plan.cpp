@@ -727,6 +727,44 @@ cwo_status run_items(cwo_plan* p, const void* in, long long in_stride, void* out
 
 }  // namespace
 
+// The GS loop with the field kept in the intermediate between propagations: propagation k of the
+// 2I + 1 (+z for even k, the adjoint for odd k) is a column pass between two row passes, and
+// the inverse row pass of k with its constraint (phase after +z, amplitude after -z) and the
+// forward row pass of k + 1 run as one kernel (launch_row_turn); only the last propagation
+// writes the field.  Buffers are checked by the caller.
+cwo_status gs_fused(cwo_plan* p, const float* amplitude, float2* u, int batch, int iterations, cudaStream_t s) {
+    cwo_status st = ensure_scratch(p, batch);
+    if (st) return st;
+    cwo::HParams hp = base_hparams(p, nullptr, 1);
+    hp.ax = p->ax; hp.ay = p->ay; hp.kf = p->kf; hp.hx = p->hx; hp.hy = p->hy;
+    hp.x_item_stride = 0; hp.y_item_stride = 0; hp.kf_item_stride = 0;
+    if (p->hcache) {
+        hp.mode = cwo::HMODE_TABLE;
+        hp.hcache = p->hcache;
+        hp.hcache_stride = p->py;
+    }
+    const long long field = (long long)p->nx * p->ny, wstride = (long long)p->ny * p->px;
+    const float scale = (float)(1.0 / ((double)p->px * (double)p->py));
+    cwo::Epilogue ph, am;
+    ph.mode = cwo::EPI_PHASE;
+    am.mode = cwo::EPI_AMPLITUDE;
+    am.amp = amplitude;
+    cudaError_t e = cwo::launch_row_fwd(p->px, u, field, &p->wmap_f, 0, p->ny, batch, p->tw_x, p->status, s);
+    if (e) return cuda_fail(e, "row forward launch");
+    const int props = 2 * iterations + 1;
+    for (int k = 0; k < props; ++k) {
+        hp.conj = k & 1;
+        if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, batch, p->tw_y, hp, s)))
+            return cuda_fail(e, "column launch");
+        if (k + 1 < props)
+            e = cwo::launch_row_turn(p->px, &p->wmap_f, p->ny, batch, field, scale, p->tw_x, p->status, (k & 1) ? am : ph, s);
+        else
+            e = cwo::launch_row_inv(p->px, &p->wmap_i, 0, u, field, p->ny, batch, scale, p->tw_x, p->status, s, ph);
+        if (e) return cuda_fail(e, "row pass launch");
+    }
+    return CWO_OK;
+}
+
 // ------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------
@@ -975,12 +1013,16 @@ cwo_status cwo_gs_run(cwo_plan* plan, const float* amplitude, void* field_c64, f
         (st = check_device_range(amplitude, n * sizeof(float), plan->device, "amplitude")) ||
         (intensity && (st = check_device_range(intensity, n * sizeof(float), plan->device, "intensity"))))
         return st;
-    // hologram plane: propagate the object field by +z and keep the phase (the kinoform)
-    st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, false, ph, true);
-    for (int i = 0; i < iterations && st == CWO_OK; ++i) {
-        // back to the object plane (conj(H) = H(-z)), amplitude constraint; forward, phase constraint
-        st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, true, am, true);
-        if (st == CWO_OK) st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, false, ph, true);
+    if (cwo::row_turn_supported(plan->px)) {
+        st = gs_fused(plan, amplitude, (float2*)field_c64, batch, iterations, (cudaStream_t)cuda_stream);
+    } else {
+        // hologram plane: propagate the object field by +z and keep the phase (the kinoform)
+        st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, false, ph, true);
+        for (int i = 0; i < iterations && st == CWO_OK; ++i) {
+            // back to the object plane (conj(H) = H(-z)), amplitude constraint; forward, phase constraint
+            st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, true, am, true);
+            if (st == CWO_OK) st = run(plan, field_c64, f, field_c64, batch, nullptr, cuda_stream, false, ph, true);
+        }
     }
     if (st == CWO_OK && intensity) st = run(plan, field_c64, f, nullptr, batch, nullptr, cuda_stream, true, in, true);
     return st;

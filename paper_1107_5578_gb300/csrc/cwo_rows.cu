@@ -431,6 +431,81 @@ k_row_inv_pp(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __r
     }
 }
 
+// Turn (P <= 4096): the inverse row pass of one propagation and the forward row pass of the next
+// in one kernel, for loops that constrain the field between propagations (the GS iteration of
+// Section "GS algorithm").  A CTA loads its R rows of the intermediate by TMA, takes their
+// inverse FFTs, crops to the Nx kept samples, scales, applies the constraint (EPI_PHASE or
+// EPI_AMPLITUDE), zero-pads and takes the forward FFTs, and stores the R rows back into the same
+// place of the intermediate by TMA (in place: no other CTA touches these rows).  The inverse
+// ends with register e of thread t at position t + e T, which is where the forward's first
+// stage takes its inputs, so the crop, constraint and padding act on the registers and no
+// exchange is added; each row's arithmetic is that of k_row_inv_p followed by k_row_fwd_p, so
+// the loop computes bit for bit what the separate passes compute through the stored field.
+template <int P, int R, int EPI>
+__global__ void __launch_bounds__(R * (P / 16))
+k_row_turn(const __grid_constant__ CUtensorMap wmap, int groups_per_item, long long field_item_stride,
+           float scale, const float4* __restrict__ tw, int* status, const Epilogue ep) {
+    pdl_wait();
+    constexpr int T = P / 16, N = P / 2, NT = R * T;
+    constexpr int BOX = P < kTmaBoxCols ? P : kTmaBoxCols;
+    static_assert(Geo<P>::NST >= 2, "at least two stages");
+    extern __shared__ __align__(1024) float2 sm[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + row_smem_words<P, R>());   // after the tile
+    const int r = threadIdx.x % R, t = threadIdx.x / R;
+    const int g = blockIdx.x, item = g / groups_per_item, y0 = (g % groups_per_item) * R;
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        mbar_arrive_expect_tx(mbar, (unsigned)(R * P * sizeof(float2)));
+#pragma unroll 1
+        for (int b = 0; b < P / BOX; ++b) tma_load_3d(sm + b * BOX * R, &wmap, mbar, y0, b * BOX, item);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(mbar, 0, status);
+    float2 v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = sm[e * NT + threadIdx.x];
+    if (__syncthreads_or(!ok)) return;         // a copy did not land: the status word says so
+    const TwTable<P> twt{tw, t};
+    inv1_to_stage0<P, R, Geo<P>::NST - 1>(v, sm, r, t, twt);
+    twt.template apply<0, true>(v);
+    stage_butterflies<P, 0, true, 16>(v);
+    const long long base = item * field_item_stride + (long long)(y0 + r) * N;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = epilogue_value<EPI>(ep, base + t + e * T, cscale(v[e], scale));
+#pragma unroll
+    for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);   // zero padding of the next transform
+    // forward: the first exchange writes the positions this thread read in the last one
+    fwd1_from<P, R, 0, 8>(v, sm, r, t, twt);
+    __syncthreads();   // every exchange read done before the tile (which aliases the region) is written
+#pragma unroll
+    for (int e = 0; e < 16; ++e) sm[e * NT + threadIdx.x] = v[e];
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll 1
+        for (int b = 0; b < P / BOX; ++b) tma_store_3d(&wmap, sm + b * BOX * R, y0, b * BOX, item);
+        tma_store_commit_and_drain();
+    }
+}
+
+template <int P, int EPI>
+static cudaError_t row_turn_impl(const CUtensorMap* wmap, int ny, int items, long long field_item_stride, float scale,
+                                 const float4* tw, int* status, const Epilogue& ep, cudaStream_t st) {
+    if constexpr (P > 4096 || P < 64) {
+        return cudaErrorNotSupported;
+    } else {
+        constexpr int R = rows_fwd<P>();
+        constexpr int T = P / 16;
+        if (ny % R || items < 1 || !status) return cudaErrorInvalidValue;
+        const size_t smem = row_smem_words<P, R>() * sizeof(float2) + sizeof(uint64_t);
+        cudaError_t e = kernel_setup<k_row_turn<P, R, EPI>>(smem, R * T, nullptr);
+        if (e != cudaSuccess) return e;
+        const int groups = ny / R;
+        return pdl_launch(k_row_turn<P, R, EPI>, dim3((unsigned)(groups * items)), dim3(R * T), smem, st, *wmap, groups,
+                          field_item_stride, scale, tw, status, ep);
+    }
+}
+
 template <int P, bool PRE, bool BULK>
 static cudaError_t row_fwd_c_launch(const float2* in, long long in_item_stride, const CUtensorMap* wmap, int item_off,
                                     int ny, int items, const float4* tw, int* status, const Prefactor& pre,
@@ -611,6 +686,24 @@ cudaError_t launch_row_inv(int px, const CUtensorMap* wmap, int item_off, float2
         CWO_P_CASES(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
+    }
+}
+
+// a CTA of at least one whole warp; above Px = 2048 the persistent row passes, which overlap one
+// group's memory traffic with another's transforms, are as fast as the turn (GS at 2048^2,
+// 40 iterations: 10.72 ms fused, 10.68 ms separate; 512^2: 1.09 against 1.30 ms)
+bool row_turn_supported(int px) { return px >= 64 && px <= 2048; }
+
+cudaError_t launch_row_turn(int px, const CUtensorMap* wmap, int ny, int items, long long field_item_stride, float scale,
+                            const float4* tw, int* status, const Epilogue& ep, cudaStream_t st) {
+    if (ep.mode != EPI_PHASE && ep.mode != EPI_AMPLITUDE) return cudaErrorInvalidValue;
+    switch (px) {
+#define CASE(P) case P: return ep.mode == EPI_PHASE \
+        ? row_turn_impl<P, EPI_PHASE>(wmap, ny, items, field_item_stride, scale, tw, status, ep, st) \
+        : row_turn_impl<P, EPI_AMPLITUDE>(wmap, ny, items, field_item_stride, scale, tw, status, ep, st);
+        CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024) CASE(2048) CASE(4096)
+#undef CASE
+        default: return cudaErrorNotSupported;
     }
 }
 

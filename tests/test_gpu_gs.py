@@ -73,15 +73,16 @@ def test_gs_run_against_oracle(mods, n, iters):
     assert np.linalg.norm(got_i - int_o) / np.linalg.norm(int_o) <= 1e-3
 
 
-@pytest.mark.parametrize("n,iters", [(128, 4), (512, 3)])
+@pytest.mark.parametrize("n,iters", [(128, 4), (512, 3), pytest.param(1024, 2, marks=pytest.mark.slow)])
 def test_gs_each_iteration_against_oracle_step(mods, n, iters):
     """Every GS iterate of the device loop checked against one oracle step taken from it
     (Section "GS algorithm": -z, amplitude constraint, +z, phase constraint).  The two plain
     propagations of each step are compared at the 2e-5 relative-L2 bar; each constraint's output
     has the required amplitude to 1e-6 and the oracle's phase within 2e-4 rad wherever the
-    propagated value exceeds 1e-3 of its maximum; and the fused ``cwo_gs_run`` after k + 1
-    iterations equals the step-by-step composition bit for bit, so the bar holds for every
-    iterate of the loop itself.  512^2 is a size of Table tbl:gs."""
+    propagated value exceeds 1e-3 of its maximum; and ``cwo_gs_run`` after k + 1 iterations --
+    which keeps the field in the intermediate and turns from one propagation to the next in one
+    kernel -- equals the step-by-step composition bit for bit, so the bar holds for every
+    iterate of the loop itself.  512^2 and 1024^2 are sizes of Table tbl:gs."""
     torch, cwo, _ = mods
     dx, lam, z = 10e-6, 633e-9, 0.1
     amp, f0 = synth.gs_problem(n, seed=21)
