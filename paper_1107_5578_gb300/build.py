@@ -14,7 +14,7 @@ LIB = os.path.join(HERE, "libcwo_gb300.so")
 
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["cwo_rows.cu", "cwo_cols.cu", "cwo_cols_a.cu", "cwo_cols_b.cu", "cwo_cols_c.cu", "cwo_noalloc.cu", "cwo_fourier.cu", "cwo_lines.cu", "cwo_copy.cu", "cwo_calib.cu"]
+CU_SOURCES = ["cwo_rows.cu", "cwo_rows_inv_a.cu", "cwo_rows_inv_b.cu", "cwo_rows_turn.cu", "cwo_cols.cu", "cwo_cols_a.cu", "cwo_cols_b.cu", "cwo_cols_c.cu", "cwo_noalloc.cu", "cwo_fourier.cu", "cwo_lines.cu", "cwo_copy.cu", "cwo_calib.cu"]
 CPP_SOURCES = ["cwo_plan.cpp", "cwo_tables.cpp", "cwo_emu.cpp", "cwo_serve.cpp"]
 
 
