@@ -289,12 +289,12 @@ __device__ __forceinline__ void xsync(int cp) {
 }
 
 // The same exchanges for R transforms of one value per thread, interleaved over the lanes
-// (thread = r + R t, PadLayout<P, R>), all of the CTA's threads in step: a stage-S block is
+// (thread = r + R t, PadLayout<P, R>), the CTA's R * P/16 threads all in step: a stage-S block is
 // stride(S) threads of each of the R transforms, i.e. stride(S) * R consecutive lanes, so the
-// barrier is warp-wide where that fits in a warp and CTA-wide otherwise.
+// barrier is warp-wide where that fits in a warp of a CTA of whole warps, and CTA-wide otherwise.
 template <int P, int R, int S>
 __device__ __forceinline__ void xsync_r() {
-    if constexpr (Geo<P>::stride(S) * R <= 32) __syncwarp();
+    if constexpr (Geo<P>::stride(S) * R <= 32 && R * (P / 16) % 32 == 0) __syncwarp();
     else __syncthreads();
 }
 

@@ -41,7 +41,8 @@ k_fourier_rows(const float2* __restrict__ in, long long in_item_stride, const __
     float2 v[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = cmul(src[t + e * T], cmul(__ldg(pre_x + t + e * T), cy));
-    fwd_from<P, R, PadLayout<P, R>, 0, 16, 0>(v, sm, r, t, TwTable<P>{tw, t});
+    fwd1_from<P, R, 0, 16>(v, sm, r, t, TwTable<P>{tw, t});
+    __syncthreads();   // every exchange read done before the tile (which aliases the region) is written
 #pragma unroll
     for (int e = 0; e < 16; ++e) sm[e * NT + threadIdx.x] = v[e];
     fence_proxy_async_smem();
@@ -68,7 +69,7 @@ k_fourier_cols(const float2* __restrict__ win, long long win_item_stride, float2
     float2 v[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = src[t + e * T];
-    fwd_from<P, C, PadLayout<P, C>, 0, 16, 0>(v, smc, c, t, TwTable<P>{tw, t});
+    fwd1_from<P, C, 0, 16>(v, smc, c, t, TwTable<P>{tw, t});
     const float2 hx = __ldg(post_x + col);
     float2* dst = out + item * out_item_stride + col;
 #pragma unroll
