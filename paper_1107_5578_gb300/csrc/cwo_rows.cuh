@@ -74,7 +74,8 @@ k_row_fwd(const float2* __restrict__ in, long long in_item_stride, const __grid_
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = cmul(v[e], cmul(__ldg(pre.fx + t + e * T), fy));
     }
-    fwd_from<P, R, PadLayout<P, R>, 0, 8, 0>(v, sm, r, t, TwTable<P>{tw, t});
+    fwd1_from<P, R, 0, 8>(v, sm, r, t, TwTable<P>{tw, t});
+    if constexpr (Geo<P>::NST > 1) __syncthreads();   // every exchange read done before the tile is written
     // dense tile [st][r]: register e of (r, t) is storage column st = e T + t of row y0 + r
 #pragma unroll
     for (int e = 0; e < 16; ++e) sm[e * NT + threadIdx.x] = v[e];
