@@ -46,7 +46,6 @@ k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restr
       long long wout_item_stride, const float4* __restrict__ tw, const HParams hp) {
     pdl_wait();
     constexpr int T = P / 16, NY = P / 2;
-    using Lay = PadLayout<P, C>;
     extern __shared__ float2 sm[];
     const int t = threadIdx.x % T, c = threadIdx.x / T;
     const int col = blockIdx.x * C + c;
@@ -58,9 +57,9 @@ k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restr
 #pragma unroll
     for (int e = 8; e < 16; ++e) v[e] = make_float2(0.f, 0.f);   // zero padding rows
     const TwTable<P> twt{tw, t};
-    fwd_from<P, C, Lay, 0, 8, 0>(v, sm, c, t, twt);
+    fwd1_from<P, C, 0, 8, false>(v, sm, c, t, twt);
     apply_h<P, 1, MIXED>(v, v, col, t, item, hp);
-    inv_from<P, C, Lay, Geo<P>::NST - 1, 0, 0>(v, sm, c, t, twt);
+    inv1_from<P, C, Geo<P>::NST - 1, false>(v, sm, c, t, twt);
     float2* dst = wout + item * wout_item_stride + (long long)col * NY;
 #pragma unroll
     for (int e = 0; e < 8; ++e) dst[t + e * T] = v[e];           // crop: rows < Ny
@@ -153,7 +152,6 @@ k_col_stack(const float2* __restrict__ win, float2* __restrict__ wout, long long
             const float4* __restrict__ tw, const HParams hp) {
     pdl_wait();
     constexpr int T = P / 16, NY = P / 2;
-    using Lay = PadLayout<P, C>;
     extern __shared__ float2 sm[];
     const int t = threadIdx.x % T, c = threadIdx.x / T;
     const int col = blockIdx.x * C + c;
@@ -164,14 +162,16 @@ k_col_stack(const float2* __restrict__ win, float2* __restrict__ wout, long long
 #pragma unroll
     for (int e = 8; e < 16; ++e) spec[e] = make_float2(0.f, 0.f);
     const TwTable<P> twt{tw, t};
-    fwd_from<P, C, Lay, 0, 8, 0>(spec, sm, c, t, twt);
+    fwd1_from<P, C, 0, 8, false>(spec, sm, c, t, twt);
 #pragma unroll 1
     for (int z = 0; z < nplanes; ++z) {
         float2 v[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) v[e] = spec[e];
         apply_h<P, 1>(v, v, col, t, z, hp);
-        inv_from<P, C, Lay, Geo<P>::NST - 1, 0, 0>(v, sm, c, t, twt);
+        // the previous plane's last exchange reads are done before this plane's first writes
+        if (z > 0) __syncthreads();
+        inv1_from<P, C, Geo<P>::NST - 1, false>(v, sm, c, t, twt);
         float2* dst = wout + z * wout_item_stride + (long long)col * NY;
 #pragma unroll
         for (int e = 0; e < 8; ++e) dst[t + e * T] = v[e];

@@ -208,22 +208,6 @@ struct TileLayout {
 };
 
 #ifdef __CUDACC__
-// Write the registers at the positions of stage SW, read them back at the positions of stage SR.
-// PING = 0: one buffer, a barrier after the write and another after the read.
-// PING = 1: exchange number XNUM uses buffer XNUM % 2 of two consecutive buffers and needs no
-//           trailing barrier (a buffer is rewritten only two exchanges later, after every
-//           thread has passed the barrier of the exchange in between).
-template <int P, int C, class Lay, int SW, int SR, int PING, int XNUM>
-__device__ __forceinline__ void exchange(float2* __restrict__ sm, int c, int t, float2 (&v)[16]) {
-    float2* b = PING ? sm + (XNUM & 1) * Lay::WORDS : sm;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) b[Lay::addr(c, stage_pos<P, SW>(t, e))] = v[e];
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = b[Lay::addr(c, stage_pos<P, SR>(t, e))];
-    if (!PING) __syncthreads();
-}
-
 // Inter-stage twiddles W_{L_s}^{(t % S_s) k'}, k' = 1..15, of stage s < NST-1.
 // TwTable: per stage a block of 8 S_s float4 laid out [kp][j], kp = 0..7, j = t mod S_s, holding
 //          the pair (W^{j (2kp+1)}, W^{j (2kp+2)}): 8 16-byte loads per thread and stage.  Only
@@ -265,7 +249,7 @@ __device__ __forceinline__ void twiddle2(float2 (&a)[16], float2 (&b)[16], const
     }
 }
 
-// ---- exchanges without trailing barriers
+// ---- exchanges with one barrier each
 // The positions a thread reads in one exchange (its positions at the stage being entered) are
 // exactly the positions it writes in the next exchange (it leaves that stage from the same
 // positions), whether the next exchange continues the same transform, turns from the forward to
@@ -288,45 +272,48 @@ __device__ __forceinline__ void xsync(int cp) {
     }
 }
 
-// The same exchanges for R transforms of one value per thread, interleaved over the lanes
-// (thread = r + R t, PadLayout<P, R>), the CTA's R * P/16 threads all in step: a stage-S block is
-// stride(S) threads of each of the R transforms, i.e. stride(S) * R consecutive lanes, so the
-// barrier is warp-wide where that fits in a warp of a CTA of whole warps, and CTA-wide otherwise.
-template <int P, int R, int S>
+// The same exchanges for R transforms of one value per thread (PadLayout<P, R>), the CTA's
+// R * P/16 threads all in step.  IL: the transforms are interleaved over the lanes (thread =
+// r + R t), so a stage-S block is stride(S) threads of each transform, stride(S) * R consecutive
+// lanes; otherwise each transform has T consecutive threads (thread = t + T r) and a block is
+// stride(S) consecutive lanes.  The barrier is warp-wide where the block fits in a warp of a CTA
+// of whole warps, and CTA-wide otherwise.
+template <int P, int R, int S, bool IL = true>
 __device__ __forceinline__ void xsync_r() {
-    if constexpr (Geo<P>::stride(S) * R <= 32 && R * (P / 16) % 32 == 0) __syncwarp();
+    constexpr int lanes = IL ? Geo<P>::stride(S) * R : Geo<P>::stride(S);
+    if constexpr (lanes <= 32 && R * (P / 16) % 32 == 0) __syncwarp();
     else __syncthreads();
 }
 
-template <int P, int R, int SW, int SR>
+template <int P, int R, int SW, int SR, bool IL = true>
 __device__ __forceinline__ void xch1(float2* __restrict__ sm, int r, int t, float2 (&v)[16]) {
     using Lay = PadLayout<P, R>;
 #pragma unroll
     for (int e = 0; e < 16; ++e) sm[Lay::addr(r, stage_pos<P, SW>(t, e))] = v[e];
-    xsync_r<P, R, (SW < SR ? SW : SR)>();
+    xsync_r<P, R, (SW < SR ? SW : SR), IL>();
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = sm[Lay::addr(r, stage_pos<P, SR>(t, e))];
 }
 
 // forward DIF from stage S to the end / adjoint from stage S down to stage 0 (or, for
 // inv1_to_stage0, down to and including the exchange into stage 0), with xch1 exchanges
-template <int P, int R, int S, int NZ0, class Tw>
+template <int P, int R, int S, int NZ0, bool IL = true, class Tw>
 __device__ __forceinline__ void fwd1_from(float2 (&v)[16], float2* __restrict__ sm, int r, int t, const Tw& tw) {
     stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(v);
     if constexpr (S < Geo<P>::NST - 1) {
         tw.template apply<S, false>(v);
-        xch1<P, R, S, S + 1>(sm, r, t, v);
-        fwd1_from<P, R, S + 1, NZ0>(v, sm, r, t, tw);
+        xch1<P, R, S, S + 1, IL>(sm, r, t, v);
+        fwd1_from<P, R, S + 1, NZ0, IL>(v, sm, r, t, tw);
     }
 }
 
-template <int P, int R, int S, class Tw>
+template <int P, int R, int S, bool IL = true, class Tw>
 __device__ __forceinline__ void inv1_from(float2 (&v)[16], float2* __restrict__ sm, int r, int t, const Tw& tw) {
     if constexpr (S < Geo<P>::NST - 1) tw.template apply<S, true>(v);
     stage_butterflies<P, S, true, 16>(v);
     if constexpr (S > 0) {
-        xch1<P, R, S, S - 1>(sm, r, t, v);
-        inv1_from<P, R, S - 1>(v, sm, r, t, tw);
+        xch1<P, R, S, S - 1, IL>(sm, r, t, v);
+        inv1_from<P, R, S - 1, IL>(v, sm, r, t, tw);
     }
 }
 
@@ -440,31 +427,6 @@ __device__ __forceinline__ void inv2x_from(float2 (&a)[16], float2 (&b)[16], flo
     if constexpr (S > 0) {
         xch2<P, CP, Lay, S, S - 1>(sm, cp, t, a, b);
         inv2x_from<P, CP, Lay, S - 1>(a, b, sm, cp, t, tw);
-    }
-}
-
-// forward DIF from stage S to the end; the registers enter holding stage-S input positions
-template <int P, int C, class Lay, int S, int NZ0, int PING, class Tw>
-__device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ sm, int c, int t, const Tw& tw) {
-    using G = Geo<P>;
-    stage_butterflies<P, S, false, (S == 0 ? NZ0 : 16)>(v);
-    if constexpr (S < G::NST - 1) {
-        tw.template apply<S, false>(v);
-        exchange<P, C, Lay, S, S + 1, PING, S>(sm, c, t, v);
-        fwd_from<P, C, Lay, S + 1, NZ0, PING>(v, sm, c, t, tw);
-    }
-}
-
-// adjoint (inverse DIT) from stage S down to stage 0; the registers enter holding stage-S
-// positions.  XOFF numbers its exchanges after those of a preceding forward transform.
-template <int P, int C, class Lay, int S, int PING, int XOFF, class Tw>
-__device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ sm, int c, int t, const Tw& tw) {
-    using G = Geo<P>;
-    if constexpr (S < G::NST - 1) tw.template apply<S, true>(v);
-    stage_butterflies<P, S, true, 16>(v);
-    if constexpr (S > 0) {
-        exchange<P, C, Lay, S, S - 1, PING, XOFF + (G::NST - 1 - S)>(sm, c, t, v);
-        inv_from<P, C, Lay, S - 1, PING, XOFF>(v, sm, c, t, tw);
     }
 }
 

@@ -68,16 +68,17 @@ k_line_conv(const float2* __restrict__ in, long long in_item_stride, const __gri
         for (int e = 0; e < 8; ++e) v[e] = cmul(v[e], __ldg(pre + t + e * T));
     }
     const TwTable<P> twt{tw, t};
-    fwd_from<P, R, PadLayout<P, R>, 0, 8, 0>(v, sm, r, t, twt);
+    fwd1_from<P, R, 0, 8>(v, sm, r, t, twt);
     const float2* hh = h + item * h_item_stride + t;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         const float2 w = __ldg(hh + e * T);
         v[e] = conj ? cmulc(v[e], w) : cmul(v[e], w);
     }
-    inv_from<P, R, PadLayout<P, R>, Geo<P>::NST - 1, 0, 0>(v, sm, r, t, twt);
+    inv1_from<P, R, Geo<P>::NST - 1>(v, sm, r, t, twt);
     // kept positions t + e T (e < 8): tile index (t + e T) R + r = e R T + threadIdx.x; the
-    // exchange region is free after the trailing barrier of the last exchange
+    // tile aliases the exchange region, so every exchange read completes first
+    __syncthreads();
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const float2 w = cscale(v[e], scale);

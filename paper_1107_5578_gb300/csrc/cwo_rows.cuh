@@ -112,7 +112,7 @@ k_row_inv(const __grid_constant__ CUtensorMap wmap, int item_off, float2* __rest
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = sm[e * NT + threadIdx.x];
     if (__syncthreads_or(!ok)) return;             // a copy did not land: the status word says so
-    inv_from<P, R, PadLayout<P, R>, Geo<P>::NST - 1, 0, 0>(v, sm, r, t, TwTable<P>{tw, t});
+    inv1_from<P, R, Geo<P>::NST - 1>(v, sm, r, t, TwTable<P>{tw, t});
     const long long base = item * out_item_stride + (long long)(y0 + r) * N;
 #pragma unroll
     for (int e = 0; e < 8; ++e) epilogue_store<EPI>(out, ep, base + t + e * T, t + e * T, y0 + r, cscale(v[e], scale));   // crop
