@@ -35,11 +35,9 @@ template <int P> constexpr int cols_per_block() {
     return c < 1 ? 1 : (c > 16 ? 16 : c);
 }
 template <int P> constexpr int col_min_blocks() { return (P / 16) * cols_per_block<P>() <= 256 ? 2 : 1; }
-// the paired kernel holds 32 values per thread (128 registers): two 256-thread CTAs per SM up to
+// The paired kernel holds 32 values per thread (128 registers): two 256-thread CTAs per SM up to
 // P = 4096, one 512-thread CTA at P = 8192 (measured 382 us per 4096^2 field vs 488 for the
-// single-column kernel)
-template <int P> constexpr bool col_paired() { return true; }
-// single column per transform (used where the paired kernel would not fit in registers)
+// single-column kernel).  Single column per transform: plans whose H is not even in kx.
 template <int P, int C, bool MIXED>
 __global__ void __launch_bounds__(C * (P / 16), col_min_blocks<P>())
 k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
@@ -193,7 +191,7 @@ static cudaError_t col_impl_t(const float2* win, long long win_item_stride, floa
         e = pdl_launch(k_col<P, C, MIXED>, dim3(px / C, items), dim3(C * T), smem, st, win, win_item_stride, wout,
                        wout_item_stride, tw, hp);
         if (e != cudaSuccess) return e;
-    } else if constexpr (col_paired<P>()) {
+    } else {         // H even in kx: mirror pairs
         constexpr int CP = cols_per_block<P>();
         if (hp.npairs != px / 2 + 1 || !hp.pairs) return cudaErrorInvalidValue;
         const size_t smem = (size_t)colp_smem_words<P, CP>() * sizeof(float2);
@@ -202,14 +200,6 @@ static cudaError_t col_impl_t(const float2* win, long long win_item_stride, floa
         const unsigned blocks = (unsigned)((hp.npairs + CP - 1) / CP);
         e = pdl_launch(k_colp<P, CP, MIXED>, dim3(items, blocks), dim3(CP * T), smem, st, win, win_item_stride, wout,
                        wout_item_stride, tw, hp, resident);
-        if (e != cudaSuccess) return e;
-    } else {
-        constexpr int C = cols_per_block<P>();
-        if (px % C != 0) return cudaErrorInvalidValue;
-        const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
-        if ((e = kernel_setup<k_col<P, C, MIXED>>(smem, C * T, nullptr))) return e;
-        e = pdl_launch(k_col<P, C, MIXED>, dim3(px / C, items), dim3(C * T), smem, st, win, win_item_stride, wout,
-                       wout_item_stride, tw, hp);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();

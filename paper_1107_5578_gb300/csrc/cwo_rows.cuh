@@ -549,7 +549,6 @@ static cudaError_t row_fwd_impl_t(const float2* in, long long in_item_stride, co
         if (grid > 0) {
             return pdl_launch(k_row_fwd_p<P, R, PRE>, dim3(grid), dim3(R * T), smem, st, in, in_item_stride, *wmap,
                               item_off, ny / R, groups, tw, status, pre);
-            return cudaGetLastError();
         }
     }
     const size_t smem = row_smem_words<P, R>() * sizeof(float2);
@@ -600,7 +599,6 @@ static cudaError_t row_inv_impl_e(const CUtensorMap* wmap, int item_off, float2*
         if (grid > 0) {
             return pdl_launch(k_row_inv_p<P, R, EPI>, dim3(grid), dim3(R * T), smem, st, *wmap, item_off, out,
                               out_item_stride, ny / R, groups, scale, tw, status, ep);
-            return cudaGetLastError();
         }
     }
     cudaError_t e = kernel_setup<k_row_inv<P, R, EPI>>(smem, R * T, nullptr);
