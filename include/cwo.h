@@ -213,11 +213,14 @@ typedef struct {
 
 /*
  * Mixed batch: `batch` fields of the plan's Nx x Ny, item i propagated with items[i] (type,
- * distance, wavelength, pitches), in one set of launches -- the batching step of a serving loop
- * that groups same-size requests.  The plan supplies the shape, the scratch and the FFT tables;
- * its own wavelength, pitches, distance and type are not used.  items is a HOST array; the
- * per-item transfer-function tables are computed in FP64 on the host (in parallel threads) and
- * uploaded stream-ordered.  in_batch_stride as in cwo_propagate_batch but must be > 0.
+ * distance, wavelength, pitches) -- the batching step of a serving loop that groups same-size
+ * requests.  The plan supplies the shape, the scratch and the FFT tables; its own wavelength,
+ * pitches, distance and type are not used.  items is a HOST array; the per-item
+ * transfer-function tables are computed in FP64 on the host (in parallel threads) and uploaded
+ * stream-ordered.  in_batch_stride as in cwo_propagate_batch but must be > 0.  Each contiguous
+ * run of angular-spectrum items is one set of three launches; each contiguous run of Fresnel
+ * items, the two separable line passes of a Fresnel plan (three launches instead when out is not
+ * on a 16-byte boundary), so a caller that orders its batch by type makes at most five launches.
  * Results are bit-identical to running each item alone (no arithmetic depends on the batch).
  */
 cwo_status cwo_propagate_items(cwo_plan* plan, const void* in, long long in_batch_stride, void* out,

@@ -271,9 +271,10 @@ cwo_status ensure_scratch(cwo_plan* p, int items) {
     p->scap = 0;
     cwo_status st = dev_alloc(&p->scratch, (size_t)items * p->ny * p->px, "scratch");
     if (st != CWO_OK) return st;
+    // wmap_s for every type: the mixed batches of any plan run their Fresnel items as line passes
     if ((e = cwo::make_intermediate_map(&p->wmap_f, p->scratch, p->ny, p->px, items, cwo::row_block_rows(p->px, false))) ||
         (e = cwo::make_intermediate_map(&p->wmap_i, p->scratch, p->ny, p->px, items, cwo::row_block_rows(p->px, true))) ||
-        ((p->type == CWO_FRESNEL_CONV || p->type == CWO_SHIFTED_FRESNEL) &&
+        (p->type != CWO_FRESNEL_FOURIER &&
          (e = cwo::make_intermediate_map(&p->wmap_s, p->scratch, p->ny, p->nx, items, cwo::line_block_rows(p->px)))))
         return cuda_fail(e, "tensor map of the intermediate");
     p->scap = items;
@@ -633,8 +634,10 @@ cwo_status ensure_itables(cwo_plan* p, int items) {
     return CWO_OK;
 }
 
-// the tables and scalars of one item of a mixed batch
-void item_tables(const cwo_plan* p, const cwo_item& it, float4* xt, float4* yt, cwo::ItemParams* prm) {
+// the tables and scalars of one item of a mixed batch.  lines: a Fresnel item that takes the two
+// separable line passes, whose tables are stored as P complex64 values at the start of the item's
+// rows (the line pass's layout); otherwise float4 rows (the column pass's layout).
+void item_tables(const cwo_plan* p, const cwo_item& it, float4* xt, float4* yt, cwo::ItemParams* prm, bool lines) {
     const AxisGeo gx(p->px), gy(p->py);
     if (it.type == CWO_ANGULAR) {
         asm_axis_table(gx, it.dx, it.lambda, it.z, true, xt);
@@ -645,8 +648,13 @@ void item_tables(const cwo_plan* p, const cwo_item& it, float4* xt, float4* yt, 
         std::vector<float2> hx(p->px), hy(p->py);
         make_h_tables(p->px, p->py, it.dx, it.dy, it.lambda, it.z, true, (it.flags & CWO_FLAG_LITERAL_SCALE) != 0,
                       nullptr, nullptr, hx.data(), hy.data(), nullptr);
-        for (int i = 0; i < p->px; ++i) xt[i] = make_float4(hx[i].x, hx[i].y, 0.f, 0.f);
-        for (int i = 0; i < p->py; ++i) yt[i] = make_float4(hy[i].x, hy[i].y, 0.f, 0.f);
+        if (lines) {
+            std::copy(hx.begin(), hx.end(), (float2*)xt);
+            std::copy(hy.begin(), hy.end(), (float2*)yt);
+        } else {
+            for (int i = 0; i < p->px; ++i) xt[i] = make_float4(hx[i].x, hx[i].y, 0.f, 0.f);
+            for (int i = 0; i < p->py; ++i) yt[i] = make_float4(hy[i].x, hy[i].y, 0.f, 0.f);
+        }
         prm->mode = cwo::HMODE_FRESNEL;
     }
     prm->kf = (float)(it.z / it.lambda);
@@ -685,9 +693,15 @@ cwo_status run_items(cwo_plan* p, const void* in, long long in_stride, void* out
     const size_t work = (size_t)batch * (p->px + p->py);
     const int nthreads = (int)std::min<size_t>((size_t)std::max(1u, std::thread::hardware_concurrency()),
                                                std::min<size_t>((size_t)batch, work / 8192 + 1));
+    // Route: a Fresnel convolution item takes the two separable line passes (32 N^2 bytes, as a
+    // Fresnel plan does) where the output allows their TMA stores, every other item the three
+    // passes; each contiguous run of one route is one sub-batch.  An item's result therefore does
+    // not depend on the other items of the batch.
+    const bool lines_ok = (uintptr_t)out % 16 == 0;
+    auto lines = [&](int i) { return lines_ok && items[i].type == CWO_FRESNEL_CONV; };
     auto worker = [&](int w) {
         for (int i = w; i < batch; i += nthreads)
-            item_tables(p, items[i], hx + (size_t)i * p->px, hy + (size_t)i * p->py, hp_items + i);
+            item_tables(p, items[i], hx + (size_t)i * p->px, hy + (size_t)i * p->py, hp_items + i, lines(i));
     };
     if (nthreads <= 1) {
         worker(0);
@@ -705,23 +719,51 @@ cwo_status run_items(cwo_plan* p, const void* in, long long in_stride, void* out
         return cuda_fail(e, "item table upload");
     if ((st = staging_release_after(p->istage, islot, s))) return st;
 
-    cwo::HParams hpar{};
-    hpar.mode = cwo::HMODE_ASM_POLY;   // per item, see items
-    hpar.ax = p->ix; hpar.ay = p->iy; hpar.items = p->iprm;
-    hpar.x_item_stride = p->px; hpar.y_item_stride = p->py;
-    hpar.kbx = p->kb_x; hpar.kby = p->kb_y; hpar.pairs = p->pairs_x; hpar.npairs = p->px / 2 + 1;
     const long long wstride = (long long)p->ny * p->px;
     const float scale = (float)(1.0 / ((double)p->px * (double)p->py));
     const bool timing = p->tev[0] != nullptr;
     auto mark = [&](int i) { return timing ? cudaEventRecord(p->tev[i], s) : cudaSuccess; };
-    if ((e = mark(0)) || (e = cwo::launch_row_fwd(p->px, (const float2*)in, in_stride, &p->wmap_f, 0, p->ny, batch, p->tw_x, p->status, s)) ||
-        (e = mark(1)))
-        return cuda_fail(e, "row forward launch");
-    if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, batch, p->tw_y, hpar, s)) || (e = mark(2)))
-        return cuda_fail(e, "column launch");
-    if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 0, (float2*)out, field, p->ny, batch, scale, p->tw_x, p->status, s)) ||
-        (e = mark(3)))
-        return cuda_fail(e, "row inverse launch");
+    const float2* fin = (const float2*)in;
+    float2* fout = (float2*)out;
+    if ((e = mark(0))) return cuda_fail(e, "event");
+    for (int i0 = 0; i0 < batch;) {
+        int i1 = i0 + 1;
+        while (i1 < batch && lines(i1) == lines(i0)) ++i1;
+        const int n = i1 - i0;
+        const bool last = i1 == batch;
+        if (lines(i0)) {
+            CUtensorMap omap;
+            if ((e = cwo::make_intermediate_map(&omap, fout + i0 * field, p->nx, p->ny, n, cwo::line_block_rows(p->py))))
+                return cuda_fail(e, "tensor map of the output");
+            if ((e = cwo::launch_line_conv(p->px, fin + i0 * in_stride, in_stride, &p->wmap_s, p->ny, n,
+                                           (const float2*)(p->ix + (size_t)i0 * p->px), 2LL * p->px, 0,
+                                           (float)(1.0 / p->px), p->tw_x, p->status, nullptr, nullptr, s)) ||
+                (last && (e = mark(1))) ||
+                (e = cwo::launch_line_conv(p->py, p->scratch, field, &omap, p->nx, n,
+                                           (const float2*)(p->iy + (size_t)i0 * p->py), 2LL * p->py, 0,
+                                           (float)(1.0 / p->py), p->tw_y, p->status, nullptr, nullptr, s)) ||
+                (last && (e = mark(2))))
+                return cuda_fail(e, "separable Fresnel launch");
+        } else {
+            cwo::HParams hpar{};
+            hpar.mode = cwo::HMODE_ASM_POLY;   // per item, see items
+            hpar.ax = p->ix + (size_t)i0 * p->px; hpar.ay = p->iy + (size_t)i0 * p->py; hpar.items = p->iprm + i0;
+            hpar.x_item_stride = p->px; hpar.y_item_stride = p->py;
+            hpar.kbx = p->kb_x; hpar.kby = p->kb_y; hpar.pairs = p->pairs_x; hpar.npairs = p->px / 2 + 1;
+            if ((e = cwo::launch_row_fwd(p->px, fin + i0 * in_stride, in_stride, &p->wmap_f, 0, p->ny, n, p->tw_x,
+                                         p->status, s)) ||
+                (last && (e = mark(1))))
+                return cuda_fail(e, "row forward launch");
+            if ((e = cwo::launch_col(p->py, p->scratch, wstride, p->scratch, wstride, p->px, n, p->tw_y, hpar, s)) ||
+                (last && (e = mark(2))))
+                return cuda_fail(e, "column launch");
+            if ((e = cwo::launch_row_inv(p->px, &p->wmap_i, 0, fout + i0 * field, field, p->ny, n, scale, p->tw_x,
+                                         p->status, s)))
+                return cuda_fail(e, "row inverse launch");
+        }
+        i0 = i1;
+    }
+    if ((e = mark(3))) return cuda_fail(e, "event");
     return CWO_OK;
 }
 

@@ -121,8 +121,15 @@ cwo_item item_of(const cwo_request& r) {
 // Launch one batch of requests in slot s: a single request is propagated straight from its field
 // to its output; a batch is gathered into the slot's input buffer, propagated into its output
 // buffer and scattered to the requests' outputs.
-cwo_status launch_batch(cwo_server* srv, Slot& s, const long long* tk, int b) {
+cwo_status launch_batch(cwo_server* srv, Slot& s, const long long* tk_in, int b) {
     const long long field = (long long)s.n * s.n;
+    // the batch's Fresnel requests after the others, so that cwo_propagate_items runs each route
+    // (three passes; two separable line passes for Fresnel) as one sub-batch
+    long long tk[cwo::kCopyMaxFields];
+    int nt = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < b; ++i)
+            if ((srv->tickets[tk_in[i]].req.type == CWO_FRESNEL_CONV) == (pass == 1)) tk[nt++] = tk_in[i];
     s.items.resize(b);
     for (int i = 0; i < b; ++i) s.items[i] = item_of(srv->tickets[tk[i]].req);
     cudaError_t e;
