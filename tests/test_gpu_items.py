@@ -79,6 +79,8 @@ def test_mixed_item_matches_a_plan_of_its_own(cwo):
         own = cwo.Plan(256, 256, t[3], t[4], t[2], t[1], t[0], t[5])
         r = own.propagate(x[k])
         assert float((r - y[k]).norm() / r.norm()) <= 1e-6, (k, t)
+        if t[0] == cwo.FRESNEL_CONV:   # the same two separable line passes as a Fresnel plan
+            assert torch.equal(r, y[k]), (k, t)
         own.close()
 
 
