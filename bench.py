@@ -533,6 +533,32 @@ def recalc_h_measurement(x, y, steps):
             "unit": UNIT, "passes_ms": {k: round(v / steps, 4) for k, v in zip(("row_fwd", "col_fwd_h_inv", "row_inv"), pp)}}
 
 
+def asm_4096_measurement(dev, steps, hbm_peak, batch=2):
+    """The 4096^2 angular spectrum method (padded to 8192^2; the precision study's size), batch 2,
+    transfer function materialised per plan: propagations/s, per-pass times and algorithmic
+    TB/s (80 N^2 bytes per propagation)."""
+    import torch
+    from paper_1107_5578_gb300 import cwo
+    n = 4096
+    x = torch.randn(batch, n, n, dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    plan = cwo.Plan(n, n, 3.74e-6, 3.74e-6, 532e-9, 0.2, cwo.ANGULAR, cwo.FLAG_CACHE_H)
+    plan.reserve(batch)
+    for _ in range(3):
+        plan.propagate_batch(x, out=y)
+    a, b, step_ev = timed_steps(plan, x, y, steps, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    pp = pass_sums(plan, step_ev) / steps
+    ms = a.elapsed_time(b) / steps
+    plan.close()
+    del x, y
+    torch.cuda.empty_cache()
+    gbs = 80 * n * n * batch / (ms / 1e3) / 1e9
+    return {"workload": f"asm_4096_pad8192_batch{batch}", "value": round(batch / (ms / 1e3), 2), "unit": UNIT,
+            "passes_ms": {k: round(v, 4) for k, v in zip(("row_fwd", "col_fwd_h_inv", "row_inv"), pp)},
+            "hbm_gbs_algorithmic": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm_peak, 4)}
+
+
 def fresnel_batch_measurement(x, y, steps, hbm_peak):
     """Fresnel diffraction (convolution form) of the same 16 fields of 2048^2 (532 nm, 8 um,
     z = 0.2 m): two separable line passes, 32 N^2 algorithmic bytes per propagation."""
@@ -724,6 +750,7 @@ def main():
     stack = stack_measurement(dev, peaks()[0]) if extra else None
     recalc_h = recalc_h_measurement(x, y, args.steps) if extra else None
     fresnel_b = fresnel_batch_measurement(x, y, args.steps, peaks()[0]) if extra else None
+    asm_4096 = asm_4096_measurement(dev, min(args.steps, 20), peaks()[0]) if extra else None
     gs_res = gs_measurement(dev) if extra else None
     cfg_512 = config_asm_512(dev) if extra else None
     cfg_stack = config_fresnel_stack_errors(dev) if extra else None
@@ -772,6 +799,7 @@ def main():
         "hologram": cfg_holo,
         "asm_recalc_h": recalc_h,
         "fresnel_batch": fresnel_b,
+        "asm_4096": asm_4096,
         "gs_kinoform": gs_res,
         "serving": serve,
         "serving_4x_rate": serve_high,
