@@ -124,8 +124,10 @@ def test_twiddle_tables(lib, p):
     assert off == len(tw)
 
 
-@pytest.mark.parametrize("p,pitch,lam,z", [(64, 10e-6, 633e-9, 0.05), (512, 8e-6, 532e-9, -0.3)])
+@pytest.mark.parametrize("p,pitch,lam,z", [(64, 10e-6, 633e-9, 0.05), (512, 8e-6, 532e-9, -0.3),
+                                           (8192, 3.74e-6, 532e-9, 0.011)])
 def test_fresnel_axis_dft(lib, p, pitch, lam, z):
+    # the sampled chirp (built by a product recurrence) and its radix-4/2 FP64 FFT against numpy
     d = np.where(np.arange(p) < p // 2, np.arange(p), np.arange(p) - p).astype(float)
     h = np.exp(1j * np.pi * (d * pitch) ** 2 / (lam * z))
     assert np.max(np.abs(cwo.fresnel_axis(p, pitch, lam, z) - np.fft.fft(h))) < 1e-9 * p
