@@ -5,22 +5,23 @@
 
 namespace cwo {
 
-__global__ void k_build_hcache(float2* __restrict__ out, int py, const HParams hp) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_build_hcache(float2* __restrict__ out, int py, const HParams hp, const int* __restrict__ yidx) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
-    if (i >= py) return;
+    if (o >= py) return;
+    const int i = yidx ? __ldg(yidx + o) : o;
     const int col = __ldg(hp.pairs + j).x;
     float2 h;
     if (hp.mode == HMODE_ASM_POLY) h = asm_h_reduced<true>(__ldg(hp.ax + col), __ldg(hp.ay + i), __ldg(hp.kf));
     else if (hp.mode == HMODE_ASM_EXACT) h = asm_h_reduced<false>(__ldg(hp.ax + col), __ldg(hp.ay + i), __ldg(hp.kf));
     else if (hp.mode == HMODE_ASM_FP32) h = asm_h_fp32(__ldg(hp.kbx + col), __ldg(hp.kby + i), hp);
     else h = asm_h_fp64(__ldg(hp.kbx + col), __ldg(hp.kby + i), hp.K, hp.sx, hp.sy);
-    out[(long long)j * py + i] = h;
+    out[(long long)j * py + o] = h;
 }
 
-cudaError_t launch_build_hcache(float2* out, int npairs, int py, const HParams& hp, cudaStream_t st) {
+cudaError_t launch_build_hcache(float2* out, int npairs, int py, const HParams& hp, cudaStream_t st, const int* yidx) {
     if (npairs < 1 || py < 1 || hp.mode > HMODE_ASM_FP64) return cudaErrorInvalidValue;
-    k_build_hcache<<<dim3((unsigned)((py + 255) / 256), (unsigned)npairs), 256, 0, st>>>(out, py, hp);
+    k_build_hcache<<<dim3((unsigned)((py + 255) / 256), (unsigned)npairs), 256, 0, st>>>(out, py, hp, yidx);
     return cudaGetLastError();
 }
 

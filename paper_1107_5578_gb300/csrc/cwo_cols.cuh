@@ -73,7 +73,9 @@ k_col(const float2* __restrict__ win, long long win_item_stride, float2* __restr
 // groups: the transfer-function values of a pair (the
 // cached table of a once-calculation plan) are read from HBM once and from L2 by the other items.
 // Thread 0 prefetches into L2 the columns of the CTA that will take this CTA's place (`resident`
-// CTAs later in launch order).
+// CTAs later in launch order), and in the CTA of the first item the cached H rows of its pairs.
+// At P = 8192 this kernel serves the per-element transfer functions; a cached one runs the split
+// form below.
 template <int P, int CP>
 constexpr int colp_smem_words() {
     return P >= 128 ? 2 * PairLayout<P, CP>::SLOTS : PadLayout<P, 2 * CP>::WORDS;
@@ -89,6 +91,15 @@ k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __rest
     const int t = CP == 1 ? (int)threadIdx.x : (int)threadIdx.x % T;
     const int cp = CP == 1 ? 0 : (int)threadIdx.x / T;
     if (threadIdx.x == 0) {
+        if (!MIXED && hp.mode == HMODE_TABLE && blockIdx.x == 0) {
+            // the cached H rows of this CTA's pairs, read after the forward transform: requested
+            // into L2 by the CTA of the first item, so that none of the items waits for HBM there
+            const int j0 = blockIdx.y * CP, nr = min(CP, hp.npairs - j0);
+            const float2* hrow = hp.hcache + (long long)j0 * hp.hcache_stride;
+            const long long bytes = (long long)nr * hp.hcache_stride * 8;
+            if ((((uintptr_t)hrow) & 15) == 0 && bytes % 16 == 0)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(hrow), "r"((unsigned)bytes) : "memory");
+        }
         const long long nb = (long long)blockIdx.y * gridDim.x + blockIdx.x + resident;
         if (nb < (long long)gridDim.x * gridDim.y) {
             const long long itn = nb % gridDim.x;
@@ -140,6 +151,71 @@ k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __rest
     }
 }
 
+// Column pass at Py = 8192 with the transfer function cached per plan, in split form.  A column
+// holds Ny = 4096 samples zero-padded to 8192, so its DFT is exactly the pair of 4096-point DFTs
+// of x_n (the even frequencies) and of x_n W_8192^n (the odd ones), and the cropped inverse is the
+// 4096-point inverse of the even half plus W_8192^-n times that of the odd half, for n < 4096.  A
+// thread carries both sequences of one column the way the 4096-point kernel carries a mirror pair
+// (one twiddle load for both, 128-bit exchanges): two exchanges per direction instead of the
+// three of the radix-16,16,16,2 transform, and two 256-thread CTAs per SM.  Grid (items,
+// 2 (Px/2 + 1)), item fastest: CTA row c takes side c & 1 of mirror pair c / 2 (the self-paired
+// columns kx = 0 and Px/2 once), so that the cached H row of a pair (64 KB, in the split order) is
+// read from HBM once and from L2 by the other side and the other items.  The first CTA of a pair
+// requests that row into L2 when it starts (without it the CTAs of a pair, which run at the same
+// time, all waited for HBM after their forward transforms: 354 against 301 us per 4096^2 field),
+// and thread 0 of every CTA prefetches into L2 the column of the CTA that will take its place.  The
+// column and the H row are read past L1 (ld.global.cg: each value once), which leaves L1 to the
+// twiddle and W_8192^n tables: 300 against 307 us per field.
+template <int P>
+__global__ void __launch_bounds__(P / 32, 2)
+k_col_split(const float2* __restrict__ win, long long win_item_stride, float2* __restrict__ wout,
+            long long wout_item_stride, const HParams hp, int resident) {
+    pdl_wait();
+    constexpr int Q = P / 2, T = Q / 16, NY = P / 2;
+    extern __shared__ float2 sm[];
+    float4* sx = reinterpret_cast<float4*>(sm);
+    const int t = threadIdx.x;
+    const int c = blockIdx.y, j = c >> 1;
+    const int2 pr = __ldg(hp.pairs + j);
+    if ((c & 1) && pr.y == pr.x) return;   // uniform over the CTA, before any barrier
+    if (threadIdx.x == 0) {
+        // the pair's H row, read after the forward transform: requested into L2 by the first CTA
+        // of the pair, so that none of its CTAs waits for HBM there
+        const float2* hrow = hp.hcache + (long long)j * hp.hcache_stride;
+        if (blockIdx.x == 0 && (c & 1) == 0 && (((uintptr_t)hrow) & 15) == 0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(hrow), "r"(P * 8) : "memory");
+        const long long nb = (long long)blockIdx.y * gridDim.x + blockIdx.x + resident;
+        if (nb < (long long)gridDim.x * gridDim.y) {
+            const long long itn = nb % gridDim.x;
+            const int cn = (int)(nb / gridDim.x);
+            const int2 pn = __ldg(hp.pairs + (cn >> 1));
+            const float2* pf = win + itn * win_item_stride + (long long)((cn & 1) ? pn.y : pn.x) * NY;
+            if ((((uintptr_t)pf) & 15) == 0)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(pf), "r"(NY * 8) : "memory");
+        }
+    }
+    const int col = (c & 1) ? pr.y : pr.x;
+    const long long item = blockIdx.x;
+    const float2* src = win + item * win_item_stride + (long long)col * NY;
+    float2 a[16], b[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) a[e] = __ldcg(src + t + e * T);   // n = t + e 256: every sample
+#pragma unroll
+    for (int e = 0; e < 16; ++e) b[e] = cmul(a[e], __ldg(hp.split_w + t + e * T));
+    fwd2v_from<Q, 1, 0, 16>(a, b, sx, 0, t, hp.split_tw);
+    const float2* hc = hp.hcache + (long long)j * hp.hcache_stride + t;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const float2 ha = __ldcg(hc + e * T), hb = __ldcg(hc + Q + e * T);
+        a[e] = hp.conj ? cmulc(a[e], ha) : cmul(a[e], ha);
+        b[e] = hp.conj ? cmulc(b[e], hb) : cmul(b[e], hb);
+    }
+    inv2v_from<Q, 1, Geo<Q>::NST - 1>(a, b, sx, 0, t, hp.split_tw);
+    float2* dst = wout + item * wout_item_stride + (long long)col * NY;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) dst[t + e * T] = cadd(a[e], cmulc(b[e], __ldg(hp.split_w + t + e * T)));
+}
+
 // Shared-source z-stack: the forward column transform of the source is computed once and kept
 // in registers; for each plane the kernel multiplies a copy by that plane's transfer function,
 // transforms it back and writes the plane (Section "Three-dimensional diffraction calculations":
@@ -183,6 +259,19 @@ static cudaError_t col_impl_t(const float2* win, long long win_item_stride, floa
                               const HParams& hp, cudaStream_t st) {
     constexpr int T = P / 16;
     cudaError_t e;
+    if constexpr (P == kSplitColP && !MIXED) {
+        if (hp.mode == HMODE_TABLE) {   // the cached H is stored in the split order at this Py
+            if (hp.asym || !hp.split_tw || !hp.split_w || !hp.hcache || !hp.pairs || hp.npairs != px / 2 + 1)
+                return cudaErrorInvalidValue;
+            const size_t smem = (size_t)colp_smem_words<P / 2, 1>() * sizeof(float2);
+            int resident = 0;
+            if ((e = kernel_setup<k_col_split<P>>(smem, P / 32, &resident))) return e;
+            e = pdl_launch(k_col_split<P>, dim3(items, 2 * hp.npairs), dim3(P / 32), smem, st, win, win_item_stride,
+                           wout, wout_item_stride, hp, resident);
+            if (e != cudaSuccess) return e;
+            return cudaGetLastError();
+        }
+    }
     if (hp.asym) {   // H(kx) != H(-kx): one column per transform
         constexpr int C = cols_per_block<P>();
         if (px % C != 0) return cudaErrorInvalidValue;
@@ -219,6 +308,7 @@ static cudaError_t col_stack_impl(const float2* win, float2* wout, long long wou
     constexpr int C = cols_per_block<P>();
     constexpr int T = P / 16;
     if (px % C != 0) return cudaErrorInvalidValue;
+    if (P == kSplitColP && hp.mode == HMODE_TABLE) return cudaErrorInvalidValue;   // cached H in the split order
     const size_t smem = (size_t)PadLayout<P, C>::WORDS * sizeof(float2);
     cudaError_t e;
     if ((e = kernel_setup<k_col_stack<P, C>>(smem, C * T, nullptr))) return e;

@@ -62,6 +62,11 @@ struct HParams {
     // HMODE_TABLE: H of mirror pair j = |kt_x| at axis index i along y is hcache[j * py + i]
     const float2* hcache;
     long long hcache_stride;
+    // HMODE_TABLE at Py = 8192 (k_col_split): the twiddle table of the 4096-point transform and
+    // W_8192^n for n < 4096; the hcache rows are then in the split order (index h 4096 + e 256 + t
+    // holds frequency 2 k + h, k the 4096-point frequency of register e of thread t)
+    const float4* split_tw;
+    const float2* split_w;
 };
 
 // launchers (return cudaGetLastError() after the launch)
@@ -110,8 +115,12 @@ cudaError_t launch_col_stack(int py, const float2* win, float2* wout, long long 
                              const float4* tw, const HParams& hp, cudaStream_t st);
 // Materialise the ASM transfer function of hp (modes POLY, EXACT, FP32, FP64 with the plan's
 // own tables) for every mirror pair j = 0 .. npairs-1 and axis index i < py: out[j * py + i],
-// evaluated by the same device functions as the column pass.
-cudaError_t launch_build_hcache(float2* out, int npairs, int py, const HParams& hp, cudaStream_t st);
+// evaluated by the same device functions as the column pass; with yidx (device, py entries),
+// entry i is evaluated at y axis index yidx[i] (the split order of k_col_split).
+cudaError_t launch_build_hcache(float2* out, int npairs, int py, const HParams& hp, cudaStream_t st,
+                                const int* yidx = nullptr);
+// Py of the split column pass (a transfer function cached per plan)
+constexpr int kSplitColP = 8192;
 // Fresnel diffraction in Fourier form (cwo_fourier.cu): source chirp + row FFT into the
 // [items][Px = Nx][Ny] intermediate; column FFT + destination chirp into the centred output
 // separable Fresnel line pass (cwo_lines.cu): `lines` lines of P/2 contiguous samples per item,

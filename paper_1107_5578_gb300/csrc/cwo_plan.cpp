@@ -199,6 +199,9 @@ struct cwo_plan {
     cwo_shifted_fresnel sfr{};
     // CWO_FLAG_CACHE_H: the ASM transfer function of the plan's own z, [Px/2 + 1 pairs][Py]
     float2* hcache = nullptr;
+    // with it at Py = 8192 (split column pass): the 4096-point twiddles, then W_8192^n (float2)
+    float4* split_tw = nullptr;
+    float2* split_w = nullptr;
 };
 
 namespace {
@@ -219,6 +222,7 @@ void free_plan(cwo_plan* p) {
     cudaFree(p->fst_x); cudaFree(p->frow_y);
     cudaFree(p->fpre_cx); cudaFree(p->fpre_cy); cudaFree(p->fpost_cx); cudaFree(p->fpost_cy);
     cudaFree(p->hcache);
+    cudaFree(p->split_tw);
     delete p;
 }
 
@@ -514,6 +518,8 @@ cwo_status run(cwo_plan* p, const void* in, long long in_stride, void* out, int 
             hp.mode = cwo::HMODE_TABLE;
             hp.hcache = p->hcache;
             hp.hcache_stride = p->py;
+            hp.split_tw = p->split_tw;
+            hp.split_w = p->split_w;
         }
     }
 
@@ -784,6 +790,8 @@ cwo_status gs_fused(cwo_plan* p, const float* amplitude, float2* u, int batch, i
         hp.mode = cwo::HMODE_TABLE;
         hp.hcache = p->hcache;
         hp.hcache_stride = p->py;
+        hp.split_tw = p->split_tw;
+        hp.split_w = p->split_w;
     }
     const long long field = (long long)p->nx * p->ny, wstride = (long long)p->ny * p->px;
     const float scale = (float)(1.0 / ((double)p->px * (double)p->py));
@@ -896,12 +904,32 @@ cwo_status create_impl(int nx, int ny, double dx, double dy, double lambda, doub
     if ((flags & CWO_FLAG_CACHE_H) && type == CWO_ANGULAR) {
         const int npairs = p->px / 2 + 1;
         if ((st = dev_alloc(&p->hcache, (size_t)npairs * p->py, "transfer-function cache"))) { free_plan(p); return st; }
+        int* yidx = nullptr;   // the split order of the split column pass
+        if (p->py == cwo::kSplitColP) {
+            const std::vector<float4> twq = twiddle_table(AxisGeo(p->py / 2));
+            const std::vector<float2> wn = split_phase(p->py);
+            const std::vector<int> yi = split_axis_index(p->py);
+            const size_t n4 = twq.size() + (wn.size() + 1) / 2;
+            if ((st = dev_alloc(&p->split_tw, n4, "split twiddles")) || (st = upload(p->split_tw, twq, "split twiddle upload"))) {
+                free_plan(p);
+                return st;
+            }
+            p->split_w = reinterpret_cast<float2*>(p->split_tw + twq.size());
+            if ((st = upload(p->split_w, wn, "split phase upload")) || (st = dev_alloc(&yidx, yi.size(), "split index")) ||
+                (st = upload(yidx, yi, "split index upload"))) {
+                cudaFree(yidx);
+                free_plan(p);
+                return st;
+            }
+        }
         const cwo::HParams hp = base_hparams(p, nullptr, 1);
-        if ((e = cwo::launch_build_hcache(p->hcache, npairs, p->py, hp, nullptr)) != cudaSuccess ||
+        if ((e = cwo::launch_build_hcache(p->hcache, npairs, p->py, hp, nullptr, yidx)) != cudaSuccess ||
             (e = cudaDeviceSynchronize()) != cudaSuccess) {
+            cudaFree(yidx);
             free_plan(p);
             return cuda_fail(e, "building the transfer-function cache");
         }
+        cudaFree(yidx);
     }
     *out = p;
     return CWO_OK;

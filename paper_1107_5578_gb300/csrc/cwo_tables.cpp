@@ -84,6 +84,27 @@ std::vector<int> bin_table(const AxisGeo& g) {
     return b;
 }
 
+std::vector<int> split_axis_index(int P) {
+    const AxisGeo g(P), gq(P / 2);
+    std::vector<int> where(P);
+    for (int i = 0; i < P; ++i) where[g.freq_of_idx(i)] = i;
+    std::vector<int> out(P);
+    for (int i = 0; i < P; ++i) {
+        const int h = i / gq.P, idx = i % gq.P;
+        out[i] = where[2 * gq.freq_of_idx(idx) + h];
+    }
+    return out;
+}
+
+std::vector<float2> split_phase(int P) {
+    std::vector<float2> w(P / 2);
+    for (int n = 0; n < P / 2; ++n) {
+        const double ang = -2.0 * kPi * (double)n / (double)P;
+        w[n] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    return w;
+}
+
 // Per-length caches: twiddles W_P^j (j < P/2) of the FP64 FFT, and the axis-index lists of the
 // frequency pairs {+k, -k}.  Built once per length, shared by every thread (read-only after).
 namespace {
@@ -122,8 +143,6 @@ const AxisCache& axis_cache(int P) {
 }
 }  // namespace
 
-// FP64 Stockham radix-2 FFT, forward sign, out-of-place ping-pong; real arithmetic written out
-// (no library complex multiply), twiddles from the per-length table
 // Forward DFT in FP64 (self-sorting Stockham form): one radix-2 pass when log2 n is odd, then
 // radix-4 passes.  A pass of radix r takes x[j m + k + q l' m] (q < r) to
 // y[(r j + q) m + k] = (sum_p x_p W_r^{p q}) W_n^{j q m}, with l' = l / r, for j < l', k < m.

@@ -29,6 +29,13 @@ std::vector<float4> twiddle_table(const AxisGeo& g);
 std::vector<int> bin_table(const AxisGeo& g);
 // storage columns of the frequencies +k and -k for k = 0 .. P/2 (0 and P/2 pair with themselves)
 std::vector<int2> mirror_pairs(const AxisGeo& g);
+// Split form of a zero-padded axis of P = 2Q points carrying Q samples x_n: its DFT is the pair of
+// Q-point DFTs of x_n (frequencies 2k) and of x_n W_P^n (frequencies 2k + 1).  Split axis index
+// i = h Q + idx (h = 0 even, 1 odd; idx a Q-point axis index) holds frequency 2 k(idx) + h.
+//   split_axis_index[i]: the P-point axis index (AxisGeo(P)) of the frequency at split index i
+//   split_phase[n]:      W_P^n for n < Q, correctly rounded from FP64
+std::vector<int> split_axis_index(int P);
+std::vector<float2> split_phase(int P);
 void fft64(std::vector<cd>& x);
 std::vector<cd> fresnel_axis_dft(int P, double pitch, double lambda, double z);
 cd fresnel_coeff(double dx, double dy, double lambda, double z, bool literal_scale);
