@@ -126,7 +126,7 @@ k_colp(const float2* __restrict__ win, long long win_item_stride, float2* __rest
     const float2* sb = win + item * win_item_stride + (long long)pr.y * NY;
     float2 a[16], b[16];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) { a[e] = sa[t + e * T]; b[e] = sb[t + e * T]; }
+    for (int e = 0; e < 8; ++e) { a[e] = __ldcg(sa + t + e * T); b[e] = __ldcg(sb + t + e * T); }
 #pragma unroll
     for (int e = 8; e < 16; ++e) { a[e] = make_float2(0.f, 0.f); b[e] = make_float2(0.f, 0.f); }
     if constexpr (P >= 128) {

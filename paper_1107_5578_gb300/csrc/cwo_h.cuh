@@ -124,7 +124,7 @@ __device__ __forceinline__ void eval_h(int col, int t, long long item, const HPa
         const int j = abs(__ldg(hp.kbx + col));
         const float2* hc = hp.hcache + (long long)j * hp.hcache_stride + t;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) f(e, __ldg(hc + e * T));
+        for (int e = 0; e < 16; ++e) f(e, __ldcg(hc + e * T));
     } else if (mode == HMODE_FRESNEL) {
         if (MIXED) {
             const float4 X = __ldg(hp.ax + item * hp.x_item_stride + col);
