@@ -40,7 +40,7 @@ COL_BYTES_PER_PROP = 32 * N * N      # column pass: read + write the Ny x Px int
 # batch 16, from one ncu capture of the current column kernel (profiles/asm_2048_batch16_launches.md);
 # scaled by the batch (traffic grows in proportion to the fields processed).  The column pass reads
 # the 67 MB transfer-function table of the plan once per launch besides its 16 fields.
-NCU_TRAFFIC_B16 = {"col_fwd_h_inv": 2151.98e6}
+NCU_TRAFFIC_B16 = {"col_fwd_h_inv": 2154.40e6}
 
 
 def traffic_bytes(kernel, batch):
