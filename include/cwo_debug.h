@@ -21,6 +21,16 @@ extern "C" {
  * the storage column of the 2Nx-wide intermediate.  bins: p ints, caller-owned. */
 cwo_status cwo_debug_axis_bins(int p, int* bins);
 
+/* Split order of a zero-padded axis of length p (power of two in [64, 8192]): the p-point DFT of
+ * p/2 samples x_n is, exactly, the (p/2)-point DFT of x_n at the even frequencies and that of
+ * x_n W_p^n at the odd ones.  Split index i = h (p/2) + idx (h = 0: even, 1: odd; idx a
+ * (p/2)-point axis index, see cwo_debug_axis_bins) holds frequency 2 bin(idx) + h.  The column
+ * pass at p = 8192 with a cached transfer function stores that table's rows in this order.
+ * index: p ints, the p-point axis index of the same frequency; phase_ri: p floats, W_p^n =
+ * exp(-2 pi i n / p) for n < p/2 (re, im interleaved) rounded from FP64.  Caller-owned; either
+ * may be NULL. */
+cwo_status cwo_debug_split_axis(int p, int* index, float* phase_ri);
+
 /* The length-p DFT (forward sign, unscaled) of the Fresnel impulse response sampled on the
  * padded axis, h(d) = exp(i pi (d pitch)^2 / (lambda z)), d = i for i < p/2 else i - p
  * (Eq. fre_conv_prop_d, one separable factor), in natural bin order, FP64.

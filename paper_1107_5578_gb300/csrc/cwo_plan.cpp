@@ -1134,6 +1134,19 @@ cwo_status cwo_debug_axis_bins(int p, int* bins) {
     return CWO_OK;
 }
 
+cwo_status cwo_debug_split_axis(int p, int* index, float* phase_ri) {
+    if (p < 64 || p > 8192 || (p & (p - 1))) return fail(CWO_ERR_INVALID_ARG, "bad axis length");
+    if (index) {
+        const std::vector<int> v = split_axis_index(p);
+        std::copy(v.begin(), v.end(), index);
+    }
+    if (phase_ri) {
+        const std::vector<float2> w = split_phase(p);
+        for (size_t n = 0; n < w.size(); ++n) { phase_ri[2 * n] = w[n].x; phase_ri[2 * n + 1] = w[n].y; }
+    }
+    return CWO_OK;
+}
+
 cwo_status cwo_debug_fresnel_axis(int p, double pitch, double lambda, double z, double* out_ri) {
     if (!out_ri || p < 2 || (p & (p - 1)) || !(pitch > 0) || !(lambda > 0) || z == 0.0)
         return fail(CWO_ERR_INVALID_ARG, "bad arguments");

@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
                 "cwo_last_error": ([], ctypes.c_char_p),
                 "cwo_version": ([], i),
                 "cwo_debug_axis_bins": ([i, vp], i),
+                "cwo_debug_split_axis": ([i, vp, vp], i),
                 "cwo_debug_fresnel_axis": ([i, d, d, d, vp], i),
                 "cwo_debug_twiddles": ([i, vp], i),
                 "cwo_debug_asm_axis": ([i, d, d, d, i, vp], i),
@@ -428,6 +429,14 @@ def axis_bins(p: int):
     out = np.empty(p, dtype=np.int32)
     check(lib().cwo_debug_axis_bins(p, out.ctypes.data), "cwo_debug_axis_bins")
     return out
+
+
+def split_axis(p: int):
+    import numpy as np
+    index = np.empty(p, dtype=np.int32)
+    phase = np.empty(p // 2, dtype=np.complex64)
+    check(lib().cwo_debug_split_axis(p, index.ctypes.data, phase.ctypes.data), "cwo_debug_split_axis")
+    return index, phase
 
 
 def fresnel_axis(p: int, pitch: float, wavelength: float, z: float):

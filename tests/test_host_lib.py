@@ -106,6 +106,28 @@ def test_axis_bins_are_a_permutation_matching_the_line_fft(lib, p):
     assert np.linalg.norm(y - want) / np.linalg.norm(want) < 5e-7
 
 
+@pytest.mark.parametrize("p", [64, 512, 8192])
+def test_split_axis_order_and_phase(lib, p):
+    # the split order of the column pass at P = 8192 (cached transfer function): the padded
+    # p-point DFT of p/2 samples equals the (p/2)-point DFTs of x_n and x_n W_p^n at the even and
+    # odd frequencies, and split index h p/2 + idx holds frequency 2 bin(idx) + h
+    q = p // 2
+    index, w = cwo.split_axis(p)
+    assert sorted(index.tolist()) == list(range(p))
+    bins_p, bins_q = cwo.axis_bins(p), cwo.axis_bins(q)
+    i = np.arange(p)
+    assert np.array_equal(bins_p[index], 2 * bins_q[i % q] + i // q)
+    n = np.arange(q)
+    assert np.max(np.abs(w.astype(np.complex128) - np.exp(-2j * np.pi * n / p))) < 1e-7
+    x = synth.random_field(q, seed=p + 7, ny=1)[0]
+    X = np.fft.fft(np.concatenate([x, np.zeros(q)]))
+    even, odd = np.fft.fft(x), np.fft.fft(x * w.astype(np.complex128))
+    split = np.concatenate([even[bins_q], odd[bins_q]])   # the split order
+    assert np.linalg.norm(split - X[bins_p[index]]) / np.linalg.norm(X) < 1e-6
+    assert lib.cwo_debug_split_axis(32, None, None) == cwo.ERR_INVALID_ARG
+    assert lib.cwo_debug_split_axis(96, None, None) == cwo.ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("p", [32, 256, 4096, 8192])
 def test_twiddle_tables(lib, p):
     tw = cwo.twiddles(p)          # complex64 view: per stage [kp][j] pairs (k = 2kp+1, 2kp+2)
