@@ -301,6 +301,8 @@ def test_cached_transfer_function_split_columns(cwo, nx, ny):
     if nx != ny:
         want = oracle.propagate(u, pitch, pitch, lam, z, oracle.ANGULAR)
         assert rel(to_host(b), want) <= TOL
+        want = oracle.propagate(u, pitch, pitch, lam, z, oracle.ANGULAR, oracle.ADJOINT)
+        assert rel(to_host(cache.adjoint(x)), want) <= TOL
 
 
 # ------------------------------------------------- properties at full size (no oracle output)
