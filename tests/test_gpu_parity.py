@@ -280,7 +280,7 @@ def test_cached_transfer_function(cwo, n, z, lam, pitch):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("nx,ny", [(4096, 4096), (1024, 4096)])
+@pytest.mark.parametrize("nx,ny", [(4096, 4096), (1024, 4096), (64, 4096)])
 def test_cached_transfer_function_split_columns(cwo, nx, ny):
     # at Py = 8192 a cached transfer function runs the split column pass (each zero-padded column
     # as the 4096-point DFTs of x_n and x_n W_8192^n, the cache in that order): forward, adjoint
