@@ -588,7 +588,8 @@ GS_PAPER_MS_40 = {512: 338.0, 1024: 1.19e3, 2048: 4.65e3}
 
 def gs_measurement(dev, iterations=40):
     """GS kinoform loop (Section "GS algorithm"): object = sqrt of a synthetic test image with a
-    random phase, ASM at +-0.1 m, 633 nm, 10 um; the timed region covers the first propagation,
+    random phase, ASM at +-0.1 m, 633 nm, 10 um, the plan's transfer function materialised once
+    (gs.GSProblem); the timed region covers the first propagation,
     `iterations` iterations and the final reconstruction (2 * iterations + 2 propagations), as
     the paper times its loop, with everything resident on the device."""
     import torch

