@@ -75,8 +75,10 @@ cwo_status cwo_debug_emulate_shifted_fresnel(int nx, int ny, double dx0, double 
 /* Host emulation of the CUDA passes for one [ny][nx] complex64 field (same butterflies, stage
  * positions, tables and transfer-function code, executed serially on the CPU): the three passes
  * of the angular spectrum method, the two separable line passes of the Fresnel form.  type is
- * CWO_ANGULAR or CWO_FRESNEL_CONV, flags 0 or CWO_FLAG_LITERAL_SCALE, adjoint 0/1.  in_ri and
- * out_ri: 2 nx ny floats each, caller-owned host memory.  Slow; meant for small fields. */
+ * CWO_ANGULAR or CWO_FRESNEL_CONV; flags 0, CWO_FLAG_LITERAL_SCALE (Fresnel) or CWO_FLAG_CACHE_H
+ * (angular spectrum: the column pass of a cached transfer function, which at Py = 2 ny = 8192 is
+ * the split form of cwo_debug_split_axis); adjoint 0/1.  in_ri and out_ri: 2 nx ny floats each,
+ * caller-owned host memory.  Slow; meant for small fields. */
 cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, double lambda, double z,
                              int type, unsigned flags, int adjoint, const float* in_ri, float* out_ri);
 

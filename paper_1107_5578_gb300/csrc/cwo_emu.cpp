@@ -89,6 +89,34 @@ void emu_line_inv(const float2* in, long long in_step, float2* out, long long ou
         for (int e = 0; e < 8; ++e) out[(long long)(t + e * T) * out_step] = R[t].v[e];
 }
 
+// the split column pass (k_col_split, P = 2Q): the Q samples x_n of a column (stride `step`) and
+// x_n W_P^n take the Q-point forward transforms, are multiplied by H at split index h Q + e T + t
+// (hs), take the adjoint stages, and the column becomes the even half plus W_P^-n times the odd half
+template <int Q>
+void emu_col_split(float2* col, long long step, const float2* w, const float4* twq, const std::vector<float2>& hs,
+                   bool adjoint) {
+    constexpr int T = Q / 16;
+    std::vector<Regs> A(T), B(T);
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < 16; ++e) {
+            A[t].v[e] = col[(long long)(t + e * T) * step];
+            B[t].v[e] = cmul(A[t].v[e], w[t + e * T]);
+        }
+    emu_fwd_from<Q, 0, 16>(A, twq);
+    emu_fwd_from<Q, 0, 16>(B, twq);
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < 16; ++e) {
+            const float2 ha = hs[e * T + t], hb = hs[Q + e * T + t];
+            A[t].v[e] = adjoint ? cmulc(A[t].v[e], ha) : cmul(A[t].v[e], ha);
+            B[t].v[e] = adjoint ? cmulc(B[t].v[e], hb) : cmul(B[t].v[e], hb);
+        }
+    emu_inv_from<Q, Geo<Q>::NST - 1>(A, twq);
+    emu_inv_from<Q, Geo<Q>::NST - 1>(B, twq);
+    for (int t = 0; t < T; ++t)
+        for (int e = 0; e < 16; ++e)
+            col[(long long)(t + e * T) * step] = cadd(A[t].v[e], cmulc(B[t].v[e], w[t + e * T]));
+}
+
 using LineFn = void (*)(const float2*, long long, float2*, long long, const float4*);
 
 LineFn pick_fwd(int p) {
@@ -118,7 +146,8 @@ extern "C" cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, do
     using namespace cwo::host;
     if (!in_ri || !out_ri || nx < 16 || ny < 16 || nx > 4096 || ny > 4096 || (nx & (nx - 1)) || (ny & (ny - 1)) ||
         !(dx > 0) || !(dy > 0) || !(lambda > 0) || (type != CWO_ANGULAR && type != CWO_FRESNEL_CONV) ||
-        (type == CWO_FRESNEL_CONV && z == 0.0) || (flags & ~CWO_FLAG_LITERAL_SCALE))
+        (type == CWO_FRESNEL_CONV && z == 0.0) || (flags & ~(CWO_FLAG_LITERAL_SCALE | CWO_FLAG_CACHE_H)) ||
+        ((flags & CWO_FLAG_CACHE_H) && type != CWO_ANGULAR))
         return CWO_ERR_INVALID_ARG;
     const int px = 2 * nx, py = 2 * ny;
     const AxisGeo gx(px), gy(py);
@@ -156,19 +185,39 @@ extern "C" cwo_status cwo_debug_emulate(int nx, int ny, double dx, double dy, do
         }
         return CWO_OK;
     }
+    auto h_at = [&](int c, int i) {   // H of storage column c at y axis index i (the column pass's code)
+        if (tmode == 2) return asm_h_fp64(kbx[c], kby[i], z / lambda, sx, sy);
+        return poly ? asm_h_reduced<true>(ax[c], ay[i], K) : asm_h_reduced<false>(ax[c], ay[i], K);
+    };
     std::vector<float2> W((size_t)ny * px);
     for (int y = 0; y < ny; ++y) fx(in + (size_t)y * nx, 1, W.data() + (size_t)y * px, 1, twx.data());
+    if ((flags & CWO_FLAG_CACHE_H) && py == kSplitColP) {
+        // the cached transfer function at Py = 8192: the split column pass, its H evaluated as the
+        // cache builder does (split index i at the y axis index of its frequency) for the
+        // canonical column of the mirror pair
+        constexpr int Q = kSplitColP / 2;
+        const std::vector<float4> twq = twiddle_table(AxisGeo(Q));
+        const std::vector<float2> wn = split_phase(py);
+        const std::vector<int> yi = split_axis_index(py);
+        const std::vector<int2> prs = mirror_pairs(gx);
+        std::vector<float2> hs(py);
+        for (const int2& pr : prs) {
+            for (int i = 0; i < py; ++i) hs[i] = h_at(pr.x, yi[i]);
+            emu_col_split<Q>(W.data() + pr.x, px, wn.data(), twq.data(), hs, adjoint != 0);
+            if (pr.y != pr.x) emu_col_split<Q>(W.data() + pr.y, px, wn.data(), twq.data(), hs, adjoint != 0);
+        }
+    } else {
     std::vector<float2> col(py);
     for (int c = 0; c < px; ++c) {
         fy(W.data() + c, px, col.data(), 1, twy.data());
         for (int i = 0; i < py; ++i) {
             float2 h;
             if (fresnel) h = cmul(hx[c], hy[i]);
-            else if (tmode == 2) h = asm_h_fp64(kbx[c], kby[i], z / lambda, sx, sy);
-            else h = poly ? asm_h_reduced<true>(ax[c], ay[i], K) : asm_h_reduced<false>(ax[c], ay[i], K);
+            else h = h_at(c, i);
             col[i] = adjoint ? cmulc(col[i], h) : cmul(col[i], h);
         }
         iy(col.data(), 1, W.data() + c, px, twy.data());
+    }
     }
     const float scale = (float)(1.0 / ((double)px * (double)py));
     std::vector<float2> line(nx);

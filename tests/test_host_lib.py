@@ -192,6 +192,21 @@ def test_host_emulation_of_the_kernels_matches_the_oracle(lib, nx, ny, kind, z, 
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-5
 
 
+@pytest.mark.parametrize("nx,z,pitch,lam", [(16, 0.2, 3.74e-6, 532e-9), (32, 0.05, 10e-6, 633e-9), (16, 1.0, 3.74e-6, 532e-9)])
+@pytest.mark.parametrize("adjoint", [0, 1])
+def test_host_emulation_of_the_split_column_pass_matches_the_oracle(lib, nx, z, pitch, lam, adjoint):
+    # the column pass of a cached transfer function at Py = 8192 (Ny = 4096), emulated on the
+    # host with the kernel's own butterflies, tables and split order: the zero-padded column as the
+    # 4096-point transforms of x_n and x_n W_8192^n, H read in the split order
+    ny = 4096
+    u = synth.random_field(nx, seed=nx + 5, ny=ny)
+    got = cwo.emulate(u.astype(np.complex64), pitch, pitch, lam, z, 0, cwo.FLAG_CACHE_H, adjoint)
+    want = oracle.propagate(u, pitch, pitch, lam, z, 0, oracle.ADJOINT if adjoint else 0)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-5
+    plain = cwo.emulate(u.astype(np.complex64), pitch, pitch, lam, z, 0, 0, adjoint)
+    assert np.linalg.norm(got - plain) / np.linalg.norm(plain) < 1e-6
+
+
 @pytest.mark.parametrize("n,dx,lam,z", [(256, 10e-6, 633e-9, 0.5), (512, 4e-6, 532e-9, 0.2), (64, 8e-6, 450e-9, -1.5)])
 def test_band_limit_matches_the_oracle(lib, n, dx, lam, z):
     import oracle
